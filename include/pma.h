@@ -1,0 +1,283 @@
+/*
+ * pma.h -- C ABI of the GB300 (sm_103a) domain-decomposition parabolic
+ * Monge-Ampere (DDPMA) adaptive mesh generator.
+ *
+ * Method: Sulman, Nguyen, Haynes & Huang, "Domain Decomposition Parabolic
+ * Monge-Ampere Approach for Fast Generation of Adaptive Moving Meshes".
+ * A mesh x(xi) = grad Psi(xi) on a box Omega_c (Sect. 2, Eq. AdpMesh) is the
+ * steady state of the parabolic Monge-Ampere flow
+ *     Psi_tau = log(|Omega_c| rho(grad Psi) det D^2 Psi)          (Eq. pmae)
+ * from Psi^0 = |xi|^2/2 (Eq. incond) with grad Psi . n = xi . n on the
+ * boundary (Eq. nbd).  Omega_c is split into overlapping subdomains that are
+ * advanced independently and exchange one layer of Dirichlet data per step
+ * (Sect. 3, Eq. transmission_condition3); the subdomain meshes are combined
+ * into one global mesh (Sects. 4.4-4.5).
+ *
+ * Everything here is plain C: host pointers, device pointers passed as
+ * void*, sizes and plain structs.  No exception or process exit crosses the
+ * boundary: every call returns a pma_status.
+ *
+ * Threading: one pma_ctx may be driven by one thread at a time, except that
+ * pma_submit, pma_poll and pma_wait may be called from any thread while a
+ * pma_serve_start() server thread runs.
+ *
+ * Layouts: global arrays are x-fastest, row-major over (z, y, x); a mesh is
+ * component-major: x_out[a * N + node] for a = 0..dim-1, N = prod(n[0..dim-1]).
+ */
+#ifndef PMA_H
+#define PMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMA_ABI_VERSION 1
+#define PMA_MAX_TERMS 4
+#define PMA_MAX_PARTS 32 /* subdomains per axis */
+
+/* ---------------------------------------------------------------- status */
+typedef enum {
+  PMA_OK = 0,             /* converged: residual <= tol                     */
+  PMA_NOT_CONVERGED = 1,  /* stopped at max_steps; the mesh is still valid  */
+  PMA_PENDING = 2,        /* request still running                          */
+  PMA_ERR_INVALID = -1,   /* bad argument or unsupported option             */
+  PMA_ERR_NOMEM = -2,     /* device memory budget or allocation exhausted   */
+  PMA_ERR_TANGLED = -3,   /* det D_h^2 Psi <= 0 or a non-finite value: the
+                             mesh of the last valid step is returned        */
+  PMA_ERR_TIMEOUT = -4,   /* pma_wait ran out of time                       */
+  PMA_ERR_CUDA = -5,      /* a CUDA call failed (see pma_last_error)        */
+  PMA_ERR_BUSY = -6,      /* operation not allowed in the current state     */
+  PMA_ERR_NOT_FOUND = -7  /* unknown or already released request id         */
+} pma_status;
+
+/* ------------------------------------------------------------ problem */
+
+/* Computational box Omega_c = prod_a [lo[a], hi[a]] with n[a] >= 3 nodes on
+ * axis a (Sect. 4: uniform grids such as 65x65 or 81x81x81).  Axes >= dim
+ * are ignored.                                                             */
+typedef struct {
+  int32_t dim;      /* 2 or 3 */
+  int32_t n[3];
+  double lo[3];
+  double hi[3];
+} pma_grid;
+
+/* Monitor density rho(x) (Sect. 2, Eq. edp1; Sect. 4, Eq. monitfn).
+ * Term shapes, x the physical mesh point:
+ *   PMA_TERM_BUMP : amp * exp(-width * |x - c|^2)
+ *   PMA_TERM_RING : amp * exp(-width * (|x - c|^2 - r2)^2)
+ *   PMA_TERM_SINE : amp * exp(-width * (x[axis] - c[axis]
+ *                                       - a * sin(2 pi k x[along]))^2)
+ *   PMA_TERM_BUMP1: amp * exp(-width * (x[axis] - c[axis])^2)
+ * Kinds:
+ *   PMA_MON_SUM     rho = base + sum of nterms terms
+ *   PMA_MON_PRODUCT rho = prod over terms of (base + term), separable
+ *   PMA_MON_ARCLEN_* rho = sqrt(1 + |grad u|^2) of the paper's test
+ *                    functions: BURGERS Eq. test_fn1 (eps = p0), SPIRAL
+ *                    Eq. test_fn2, TANH_SPHERE Eq. test_fn3d1, NINE_SPHERES
+ *                    Eq. test_fn3d2.  nterms is ignored.
+ * The density need not be normalised: the normalisation of Eq. (edp) is
+ * applied by the solver (see pma_params.normalize).                        */
+enum { PMA_TERM_BUMP = 0, PMA_TERM_RING = 1, PMA_TERM_SINE = 2, PMA_TERM_BUMP1 = 3 };
+enum { PMA_MON_SUM = 0, PMA_MON_PRODUCT = 1, PMA_MON_ARCLEN_BURGERS = 2,
+       PMA_MON_ARCLEN_SPIRAL = 3, PMA_MON_ARCLEN_TANH_SPHERE = 4,
+       PMA_MON_ARCLEN_NINE_SPHERES = 5 };
+
+typedef struct {
+  int32_t type;
+  int32_t axis;
+  int32_t along;
+  int32_t reserved;
+  double amp, width, r2, a, k;
+  double c[3];
+} pma_term;
+
+typedef struct {
+  int32_t kind;
+  int32_t nterms;   /* 0..PMA_MAX_TERMS */
+  double base;
+  double p0;
+  pma_term term[PMA_MAX_TERMS];
+} pma_monitor;
+
+/* Overlapping decomposition (Sect. 3).  parts[a] subdomains along axis a
+ * (slabs when one axis is split, blocks otherwise); neighbours share
+ * `overlap` node indices (>= 2 when any axis is split; Sect. 4.1 uses 3,
+ * Sect. 4.4 studies 5..15).  Core partition b_k = round(k N / p); part k
+ * spans [b_k - floor(o/2), b_{k+1} - 1 + ceil(o/2)] clipped to the grid; the
+ * owned core is [b_k, b_{k+1} - 1] and must hold >= ceil(o/2) + 1 nodes.
+ * transmission: PMA_TRANSMISSION_PARALLEL (Eq. transmission_condition3,
+ * every subdomain takes its neighbours' previous-step values) or
+ * PMA_TRANSMISSION_ALTERNATING (Algorithm 1: a subdomain takes the new value
+ * of an owner that precedes it in raster order).                           */
+enum { PMA_TRANSMISSION_PARALLEL = 0, PMA_TRANSMISSION_ALTERNATING = 1 };
+
+typedef struct {
+  int32_t parts[3];
+  int32_t overlap;
+  int32_t transmission;
+} pma_decomp;
+
+/* Pseudo-time integration and stopping (Sects. 2, 4.4).
+ *   dt          forward-Euler step (Sect. 4.4 uses 0.015..0.12 * h^2)
+ *   tol         stop when residual <= tol at a checked step
+ *   max_steps   hard cap (PMA_NOT_CONVERGED when reached)
+ *   stop_norm   PMA_STOP_MAX_UT: residual = max |Psi_tau| over updated nodes;
+ *               PMA_STOP_L2_INCREMENT: ||Psi^{n+1} - Psi^n||_2 of
+ *               Eq. (dd_stop_criterion), trapezoid rule per subdomain
+ *   stop_rule   PMA_RULE_ALL: every subdomain below tol (max);
+ *               PMA_RULE_ANY: min over subdomains (Algorithm 1, step 6)
+ *   check_every test the stop rule after every check_every steps (>= 1)
+ *   rhs         PMA_RHS_LOG (Eq. pmae) or PMA_RHS_ROOT:
+ *               (|Omega_c| rho det / theta)^(1/dim) - 1, with theta of the
+ *               previous step (same steady state)
+ *   normalize   PMA_NORM_GLOBAL_THETA: rho is normalised by
+ *               theta = sum_nodes w rho det D_h^2 Psi over the combined mesh
+ *               (the discrete int_Omega rho of Eq. edp) every step;
+ *               PMA_NORM_NONE: the subdomain equations of Eq. (pmae1a) as
+ *               printed, log(rho det D^2 Psi)
+ *   precision   PMA_FP32 (sweep in FP32, reductions and stop test in FP64)
+ *               or PMA_FP64                                                */
+enum { PMA_STOP_MAX_UT = 0, PMA_STOP_L2_INCREMENT = 1 };
+enum { PMA_RULE_ALL = 0, PMA_RULE_ANY = 1 };
+enum { PMA_RHS_LOG = 0, PMA_RHS_ROOT = 1 };
+enum { PMA_NORM_GLOBAL_THETA = 0, PMA_NORM_NONE = 1 };
+enum { PMA_FP32 = 0, PMA_FP64 = 1 };
+
+typedef struct {
+  double dt;
+  double tol;
+  int64_t max_steps;
+  int32_t stop_norm;
+  int32_t stop_rule;
+  int32_t check_every;
+  int32_t rhs;
+  int32_t normalize;
+  int32_t precision;
+} pma_params;
+
+/* Outcome of one request. */
+typedef struct {
+  int64_t steps;       /* pseudo-time steps taken                          */
+  double residual;     /* residual of the last step (stop_norm)            */
+  double theta;        /* normalisation sum of the last step               */
+  double min_det;      /* min det D_h^2 Psi over updated nodes, last step  */
+  double shift;        /* internal uniform offset already removed from Psi */
+  int32_t status;      /* pma_status of the request                        */
+  int32_t reserved;
+  double latency_us;   /* admission to completion, host clock              */
+} pma_info;
+
+typedef struct pma_ctx pma_ctx;
+
+/* ------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t, NULL = a new non-blocking stream owned by the context).
+ * mem_budget_bytes caps the device memory held by admitted requests (0 = no
+ * cap); requests beyond it wait for admission.  The context owns all device
+ * memory it allocates and frees it in pma_destroy.
+ * Errors: PMA_ERR_INVALID (NULL ctx), PMA_ERR_CUDA.                         */
+pma_status pma_create(pma_ctx **ctx, int device, size_t mem_budget_bytes, void *cuda_stream);
+
+/* Stop a running server, wait for the device and free everything. */
+pma_status pma_destroy(pma_ctx *ctx);
+
+/* Tuning knobs (no effect on results).
+ *   PMA_OPT_WINDOW_STEPS   steps per CUDA-graph window (default 32)
+ *   PMA_OPT_USE_GRAPHS     1 = capture windows in CUDA graphs (default)
+ *   PMA_OPT_LAUNCH_MODE    PMA_LAUNCH_BATCHED: all subdomains of all admitted
+ *                          requests in one launch per step (default);
+ *                          PMA_LAUNCH_PER_SUBDOMAIN: the plain reference path,
+ *                          one launch per subdomain per step, no graphs
+ *   PMA_OPT_TILE_2D        2D tile shape id (0 = auto)
+ *   PMA_OPT_TILE_3D        3D tile shape id (0 = auto)
+ *   PMA_OPT_MAX_ACTIVE     cap on concurrently admitted requests (0 = none) */
+enum { PMA_OPT_WINDOW_STEPS = 1, PMA_OPT_USE_GRAPHS = 2, PMA_OPT_LAUNCH_MODE = 3,
+       PMA_OPT_TILE_2D = 4, PMA_OPT_TILE_3D = 5, PMA_OPT_MAX_ACTIVE = 6 };
+enum { PMA_LAUNCH_BATCHED = 0, PMA_LAUNCH_PER_SUBDOMAIN = 1 };
+pma_status pma_set_option(pma_ctx *ctx, int32_t option, int64_t value);
+pma_status pma_get_option(pma_ctx *ctx, int32_t option, int64_t *value);
+
+/* ------------------------------------------------------------ requests */
+
+/* Queue one mesh-generation request.  All inputs are copied; psi0 (optional,
+ * host, N doubles, NULL = Eq. incond) is a warm start such as the previous
+ * steady state (Sect. 2).  The request is admitted to the device at the next
+ * window boundary when its memory fits the budget.
+ * Errors: PMA_ERR_INVALID (bad grid/decomposition/params), PMA_ERR_NOMEM
+ * (larger than the whole budget).                                          */
+pma_status pma_submit(pma_ctx *ctx, const pma_grid *grid, const pma_monitor *monitor,
+                      const pma_decomp *decomp, const pma_params *params,
+                      const double *psi0, uint64_t *req_id);
+
+/* Advance every admitted request on the calling thread until all queued and
+ * admitted requests are finished or max_windows windows have run (<= 0: no
+ * limit).  *n_active (optional) receives the number still unfinished.     */
+pma_status pma_run(pma_ctx *ctx, int64_t max_windows, int32_t *n_active);
+
+/* Continuous batching on a context-owned host thread: requests submitted
+ * at any time are admitted at window boundaries as memory frees up, and
+ * retire when they finish.  pma_serve_stop waits for the thread.           */
+pma_status pma_serve_start(pma_ctx *ctx);
+pma_status pma_serve_stop(pma_ctx *ctx);
+
+/* Non-blocking completion test (*done = 1 when finished). */
+pma_status pma_poll(pma_ctx *ctx, uint64_t req_id, int32_t *done);
+
+/* Block until the request finishes or timeout_us elapses (< 0: forever);
+ * PMA_ERR_TIMEOUT on expiry, otherwise the request's final status.        */
+pma_status pma_wait(pma_ctx *ctx, uint64_t req_id, int64_t timeout_us);
+
+/* Combined mesh of a finished request into caller-owned HOST memory:
+ * x_out dim*N doubles (component-major), psi_out optional N doubles
+ * (combined Psi), info optional.  Combination is owner-takes: each global
+ * node takes grad_h Psi from the subdomain whose core holds it.  Releases
+ * the request.  Returns the request's final status (PMA_OK,
+ * PMA_NOT_CONVERGED or PMA_ERR_TANGLED) or an error.                        */
+pma_status pma_get_mesh(pma_ctx *ctx, uint64_t req_id, double *x_out, double *psi_out,
+                        pma_info *info);
+
+/* Same into caller-owned DEVICE memory on the context's stream, without a
+ * host copy and without releasing: x_dev holds dim*N values of type double
+ * (out_fp64 = 1) or float (0); psi_dev optional N values of the same type.
+ * The copy is complete when the context's stream reaches it.              */
+pma_status pma_get_mesh_device(pma_ctx *ctx, uint64_t req_id, void *x_dev, int32_t out_fp64,
+                               void *psi_dev, pma_info *info);
+
+/* FP64 positivity check of a finished request: recomputes det D_h^2 Psi in
+ * FP64 at every global node (Sylvester minors of the symmetric FD Hessian)
+ * and the signed measure of every mesh cell (2 triangles per quad in both
+ * diagonal splits; 6 tetrahedra per hexahedron).  out[0] = min det,
+ * out[1] = min leading minor, out[2] = min cell measure, out[3] = number of
+ * non-positive cells.                                                     */
+pma_status pma_check_mesh(pma_ctx *ctx, uint64_t req_id, double *out4);
+
+/* Drop a request (finished or not) and free its device memory. */
+pma_status pma_release(pma_ctx *ctx, uint64_t req_id);
+
+/* Number of requests queued, admitted and finished-but-unreleased. */
+pma_status pma_counts(pma_ctx *ctx, int32_t *queued, int32_t *active, int32_t *finished);
+
+/* ------------------------------------------------------------ one shot */
+
+/* Synchronous convenience on device `device` (its own context and stream):
+ * submit, run to completion and copy the mesh to host x_out (dim*N doubles).
+ * Returns the request's final status.                                     */
+pma_status pma_solve(int device, const pma_grid *grid, const pma_monitor *monitor,
+                     const pma_decomp *decomp, const pma_params *params, const double *psi0,
+                     double *x_out, double *psi_out, pma_info *info);
+
+/* ------------------------------------------------------------ misc */
+const char *pma_status_str(int32_t status);
+/* Last CUDA / validation error text of this thread (never NULL). */
+const char *pma_last_error(void);
+int32_t pma_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMA_H */

@@ -1,0 +1,1043 @@
+// pma_host.cu -- host runtime behind the C ABI of include/pma.h.
+//
+// A context owns a CUDA stream, the device tables of every admitted request
+// (subdomain descriptors, per-class tile work lists, per-tile partial
+// records, per-problem descriptors and scalars) and the requests' state
+// buffers.  Work advances in windows of `window` forward-Euler steps: one
+// launch per kernel class and step, all captured in one CUDA graph, so a
+// window is a single graph launch.  Between windows the host reads the
+// per-problem scalars, retires finished requests, admits queued ones while
+// the memory budget allows (continuous batching), and rebuilds the tables
+// when the set of requests changed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "pma.h"
+#include "pma_internal.h"
+
+using namespace pma;
+
+namespace {
+
+thread_local std::string g_err = "";
+
+void set_err(const std::string& s) { g_err = s; }
+
+#define PMA_CK(call)                                                       \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) {                                               \
+      set_err(std::string(#call) + ": " + cudaGetErrorString(e_));         \
+      return PMA_ERR_CUDA;                                                 \
+    }                                                                      \
+  } while (0)
+
+using Clock = std::chrono::steady_clock;
+
+struct HostSub {
+  int n[3], g0[3], clo[3], chi[3], k[3];
+  int faces, idx;
+  size_t elems;
+  size_t off[2];  // byte offsets of the two buffers in the request block
+};
+
+enum ReqState { RQ_QUEUED = 0, RQ_ACTIVE = 1, RQ_FINISHED = 2 };
+
+struct Request {
+  uint64_t id = 0;
+  pma_grid g{};
+  pma_monitor m{};
+  pma_decomp d{};
+  pma_params p{};
+  std::vector<double> psi0;
+  int dim = 2, cls = 0, esize = 4;
+  int parts[3] = {1, 1, 1};
+  int bcore[3][kMaxParts + 1];
+  std::vector<HostSub> subs;
+  long long nodes = 0;       // global nodes
+  long long sub_nodes = 0;   // subdomain nodes (with overlap duplicates)
+  size_t bytes = 0;          // device bytes
+  size_t psi_off = 0;
+  char* block = nullptr;     // device allocation
+  int slot = -1;
+  ReqState state = RQ_QUEUED;
+  pma_info info{};
+  Clock::time_point t_submit, t_done;
+};
+
+// --------------------------------------------------------------- validation
+bool monitor_ok(const pma_monitor& m, int dim) {
+  if (m.kind < PMA_MON_SUM || m.kind > PMA_MON_ARCLEN_NINE_SPHERES) return false;
+  if ((m.kind == PMA_MON_ARCLEN_BURGERS || m.kind == PMA_MON_ARCLEN_SPIRAL) && dim != 2)
+    return false;
+  if ((m.kind == PMA_MON_ARCLEN_TANH_SPHERE || m.kind == PMA_MON_ARCLEN_NINE_SPHERES) &&
+      dim != 3)
+    return false;
+  if (m.kind == PMA_MON_ARCLEN_BURGERS && !(m.p0 > 0.0)) return false;
+  if (m.kind <= PMA_MON_PRODUCT) {
+    if (m.nterms < 0 || m.nterms > PMA_MAX_TERMS) return false;
+    for (int t = 0; t < m.nterms; ++t) {
+      const pma_term& q = m.term[t];
+      if (q.type < PMA_TERM_BUMP || q.type > PMA_TERM_BUMP1) return false;
+      if (q.axis < 0 || q.axis >= dim || q.along < 0 || q.along >= dim) return false;
+    }
+  }
+  return true;
+}
+
+// Core partition b_k = round(k N / p); part k spans
+// [b_k - floor(o/2), b_{k+1} - 1 + ceil(o/2)] clipped to [0, N-1].
+bool axis_parts(int n, int parts, int overlap, int* b, int* lo, int* hi) {
+  if (parts < 1 || parts > kMaxParts) return false;
+  if (parts > 1 && overlap < 2) return false;
+  const int ol = overlap / 2, oh = overlap - overlap / 2;
+  for (int k = 0; k <= parts; ++k) b[k] = (int)((2LL * k * n + parts) / (2LL * parts));
+  for (int k = 0; k < parts; ++k) {
+    lo[k] = (k == 0) ? 0 : b[k] - ol;
+    hi[k] = (k == parts - 1) ? n - 1 : b[k + 1] - 1 + oh;
+    if (parts > 1 && b[k + 1] - b[k] < oh + 1) return false;
+    if (hi[k] - lo[k] + 1 < 3) return false;
+  }
+  return true;
+}
+
+pma_status build_request(Request& r) {
+  const pma_grid& g = r.g;
+  if (g.dim < 2 || g.dim > 3) {
+    set_err("grid.dim must be 2 or 3");
+    return PMA_ERR_INVALID;
+  }
+  r.dim = g.dim;
+  const pma_params& p = r.p;
+  if (!(p.dt > 0.0) || !std::isfinite(p.dt) || p.max_steps < 0 || !(p.tol >= 0.0)) {
+    set_err("params: dt > 0, tol >= 0, max_steps >= 0 required");
+    return PMA_ERR_INVALID;
+  }
+  if (p.stop_norm < 0 || p.stop_norm > 1 || p.stop_rule < 0 || p.stop_rule > 1 || p.rhs < 0 ||
+      p.rhs > 1 || p.normalize < 0 || p.normalize > 1 || p.precision < 0 || p.precision > 1) {
+    set_err("params: option out of range");
+    return PMA_ERR_INVALID;
+  }
+  if (r.d.transmission != PMA_TRANSMISSION_PARALLEL) {
+    set_err("decomp.transmission: only the parallel form runs on the device");
+    return PMA_ERR_INVALID;
+  }
+  if (!monitor_ok(r.m, r.dim)) {
+    set_err("monitor: bad kind, term or axis");
+    return PMA_ERR_INVALID;
+  }
+  int lo[3][kMaxParts], hi[3][kMaxParts];
+  r.nodes = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (a >= r.dim) {
+      r.parts[a] = 1;
+      r.bcore[a][0] = 0;
+      r.bcore[a][1] = 1;
+      lo[a][0] = hi[a][0] = 0;
+      continue;
+    }
+    if (g.n[a] < 3 || !(g.hi[a] > g.lo[a])) {
+      set_err("grid: n >= 3 and hi > lo on every axis");
+      return PMA_ERR_INVALID;
+    }
+    r.parts[a] = r.d.parts[a] < 1 ? 1 : r.d.parts[a];
+    if (!axis_parts(g.n[a], r.parts[a], r.d.overlap, r.bcore[a], lo[a], hi[a])) {
+      set_err("decomp: parts/overlap incompatible with the grid (core >= ceil(o/2)+1)");
+      return PMA_ERR_INVALID;
+    }
+    r.nodes *= g.n[a];
+  }
+  for (int a = r.dim; a < 3; ++a)
+    for (int k = 2; k <= kMaxParts; ++k) r.bcore[a][k] = 1;
+  for (int a = 0; a < r.dim; ++a)
+    for (int k = r.parts[a] + 1; k <= kMaxParts; ++k) r.bcore[a][k] = g.n[a];
+  r.cls = (r.dim == 2) ? (p.precision == PMA_FP64 ? CLS_2D_F64 : CLS_2D_F32)
+                       : (p.precision == PMA_FP64 ? CLS_3D_F64 : CLS_3D_F32);
+  r.esize = (p.precision == PMA_FP64) ? 8 : 4;
+  r.subs.clear();
+  size_t off = 0;
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  int idx = 0;
+  for (int kz = 0; kz < r.parts[2]; ++kz)
+    for (int ky = 0; ky < r.parts[1]; ++ky)
+      for (int kx = 0; kx < r.parts[0]; ++kx, ++idx) {
+        HostSub s{};
+        const int kk[3] = {kx, ky, kz};
+        s.faces = 0;
+        for (int a = 0; a < 3; ++a) {
+          s.k[a] = kk[a];
+          s.g0[a] = lo[a][kk[a]];
+          s.n[a] = hi[a][kk[a]] - lo[a][kk[a]] + 1;
+          s.clo[a] = r.bcore[a][kk[a]] - s.g0[a];
+          s.chi[a] = r.bcore[a][kk[a] + 1] - 1 - s.g0[a];
+          if (a >= r.dim) {
+            s.clo[a] = s.chi[a] = 0;
+            s.n[a] = 1;
+          }
+          if (kk[a] == 0) s.faces |= 1 << (2 * a);
+          if (kk[a] == r.parts[a] - 1) s.faces |= 1 << (2 * a + 1);
+        }
+        s.idx = idx;
+        s.elems = (size_t)s.n[0] * s.n[1] * s.n[2];
+        r.sub_nodes += (long long)s.elems;
+        for (int b = 0; b < 2; ++b) {
+          s.off[b] = off;
+          off = align(off + s.elems * r.esize);
+        }
+        r.subs.push_back(s);
+      }
+  r.psi_off = off;
+  if (!r.psi0.empty()) off = align(off + (size_t)r.nodes * sizeof(double));
+  r.bytes = off;
+  return PMA_OK;
+}
+
+}  // namespace
+
+// ============================================================== context
+struct pma_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0, used = 0;
+  int num_sms = 1;
+
+  std::mutex mu;
+  std::condition_variable cv;
+  uint64_t next_id = 1;
+  std::map<uint64_t, std::unique_ptr<Request>> reqs;
+  std::deque<uint64_t> queue;
+  std::vector<uint64_t> active;
+
+  // slots
+  int slot_cap = 0;
+  std::vector<int> free_slots;
+  ProbDesc* d_probs = nullptr;
+  ProbState* d_state = nullptr;
+  std::vector<ProbDesc> h_probs;
+  ProbState* h_state = nullptr;  // pinned mirror
+
+  // tables
+  SubDesc* d_subs = nullptr;
+  size_t subs_cap = 0;
+  WorkItem* d_work[NUM_CLS] = {};
+  Partial* d_part[NUM_CLS] = {};
+  size_t work_cap[NUM_CLS] = {};
+  int nwork[NUM_CLS] = {};
+  int grid[NUM_CLS] = {};
+  int tile_id[NUM_CLS] = {};
+  std::vector<SubDesc> h_subs;
+  std::vector<WorkItem> h_work[NUM_CLS];
+  bool dirty = true;
+  long long dead_tiles = 0, live_tiles = 0;
+
+  // graphs
+  cudaGraphExec_t gexec = nullptr;
+  int graph_steps = 0;
+  bool graph_valid = false;
+
+  // combine scratch
+  CombineJob* d_jobs = nullptr;
+  int jobs_cap = 0;
+  double* d_check = nullptr;
+
+  // options
+  int window = 32;
+  int use_graphs = 1;
+  int launch_mode = PMA_LAUNCH_BATCHED;
+  int opt_tile2d = 0, opt_tile3d = 0;
+  int max_active = 0;
+
+  // server
+  std::thread server;
+  std::atomic<bool> stop{false};
+  bool serving = false;
+  pma_status server_err = PMA_OK;
+};
+
+namespace {
+
+pma_status ensure_slots(pma_ctx* c, int need) {
+  if (need <= c->slot_cap) return PMA_OK;
+  int cap = std::max(need, std::max(64, c->slot_cap * 2));
+  ProbDesc* np = nullptr;
+  ProbState* ns = nullptr;
+  ProbState* hs = nullptr;
+  PMA_CK(cudaMalloc(&np, sizeof(ProbDesc) * cap));
+  PMA_CK(cudaMalloc(&ns, sizeof(ProbState) * cap));
+  PMA_CK(cudaMallocHost(&hs, sizeof(ProbState) * cap));
+  PMA_CK(cudaMemsetAsync(ns, 0, sizeof(ProbState) * cap, c->stream));
+  if (c->slot_cap) {
+    PMA_CK(cudaMemcpyAsync(ns, c->d_state, sizeof(ProbState) * c->slot_cap,
+                           cudaMemcpyDeviceToDevice, c->stream));
+    PMA_CK(cudaStreamSynchronize(c->stream));
+    cudaFree(c->d_probs);
+    cudaFree(c->d_state);
+    memcpy(hs, c->h_state, sizeof(ProbState) * c->slot_cap);
+    cudaFreeHost(c->h_state);
+  }
+  for (int s = cap - 1; s >= c->slot_cap; --s) c->free_slots.push_back(s);
+  c->h_probs.resize(cap);
+  c->d_probs = np;
+  c->d_state = ns;
+  c->h_state = hs;
+  c->slot_cap = cap;
+  c->dirty = true;
+  c->graph_valid = false;
+  return PMA_OK;
+}
+
+template <typename X>
+pma_status ensure_buf(X** p, size_t* cap, size_t need) {
+  if (need <= *cap && *p) return PMA_OK;
+  size_t nc = std::max<size_t>(need, std::max<size_t>(256, *cap * 2));
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  PMA_CK(cudaMalloc(p, sizeof(X) * nc));
+  *cap = nc;
+  return PMA_OK;
+}
+
+void fill_probdesc(const Request& r, ProbDesc& pd) {
+  memset(&pd, 0, sizeof(pd));
+  pd.dim = r.dim;
+  pd.vol = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    if (a < r.dim) {
+      pd.N[a] = r.g.n[a];
+      pd.lo[a] = r.g.lo[a];
+      pd.h[a] = (r.g.hi[a] - r.g.lo[a]) / (double)(r.g.n[a] - 1);
+      pd.vol *= r.g.hi[a] - r.g.lo[a];
+    } else {
+      pd.N[a] = 1;
+      pd.lo[a] = 0.0;
+      pd.h[a] = 1.0;
+    }
+    pd.parts[a] = r.parts[a];
+    for (int k = 0; k <= kMaxParts; ++k) pd.bcore[a][k] = r.bcore[a][k];
+  }
+  pd.nsub = (int)r.subs.size();
+  pd.cls = r.cls;
+  pd.stop_norm = r.p.stop_norm;
+  pd.stop_rule = r.p.stop_rule;
+  pd.check_every = r.p.check_every > 0 ? r.p.check_every : 1;
+  pd.rhs = r.p.rhs;
+  pd.normalize = r.p.normalize;
+  pd.transmission = r.d.transmission;
+  pd.dt = r.p.dt;
+  pd.tol = r.p.tol;
+  pd.max_steps = r.p.max_steps;
+  pd.psi0 = r.psi0.empty() ? nullptr : (const double*)(r.block + r.psi_off);
+  pd.mon.kind = r.m.kind;
+  pd.mon.nterms = r.m.nterms;
+  pd.mon.base = r.m.base;
+  pd.mon.p0 = r.m.p0;
+  for (int t = 0; t < kMaxTerms; ++t) pd.mon.t[t] = r.m.term[t];
+}
+
+int pick_tile(pma_ctx* c, int cls) {
+  if (cls == CLS_2D_F32 || cls == CLS_2D_F64) {
+    int id = c->opt_tile2d;
+    return (id >= 0 && id < tile2d_count()) ? id : 0;
+  }
+  int id = c->opt_tile3d;
+  return (id >= 0 && id < tile3d_count()) ? id : 0;
+}
+
+// Rebuild subdomain table, work lists and problem descriptors for the
+// current active + finished requests.  Only active requests get tiles.
+pma_status rebuild(pma_ctx* c) {
+  c->h_subs.clear();
+  for (int k = 0; k < NUM_CLS; ++k) {
+    c->h_work[k].clear();
+    c->tile_id[k] = pick_tile(c, k);
+  }
+  c->live_tiles = 0;
+  c->dead_tiles = 0;
+  for (auto& kv : c->reqs) {
+    Request& r = *kv.second;
+    if (r.state == RQ_QUEUED || r.slot < 0) continue;
+    ProbDesc& pd = c->h_probs[r.slot];
+    fill_probdesc(r, pd);
+    pd.sub_base = (int)c->h_subs.size();
+    std::vector<WorkItem>& wl = c->h_work[r.cls];
+    const bool live = (r.state == RQ_ACTIVE);
+    pd.tile_begin = (int)wl.size();
+    int tx, ty, tz;
+    if (r.dim == 2) {
+      Tile2D t = tile2d_shape(c->tile_id[r.cls]);
+      tx = t.tx;
+      ty = t.ty;
+      tz = 1;
+    } else {
+      Tile3D t = tile3d_shape(c->tile_id[r.cls]);
+      tx = t.tx;
+      ty = t.ty;
+      tz = t.tz;
+    }
+    for (size_t si = 0; si < r.subs.size(); ++si) {
+      const HostSub& hs = r.subs[si];
+      SubDesc sd{};
+      sd.prob = r.slot;
+      for (int a = 0; a < 3; ++a) {
+        sd.n[a] = hs.n[a];
+        sd.g0[a] = hs.g0[a];
+        sd.clo[a] = hs.clo[a];
+        sd.chi[a] = hs.chi[a];
+        sd.k[a] = hs.k[a];
+      }
+      sd.faces = hs.faces;
+      sd.idx = hs.idx;
+      sd.v[0] = r.block + hs.off[0];
+      sd.v[1] = r.block + hs.off[1];
+      sd.tile_begin = (int)wl.size();
+      if (live) {
+        const int sidx = (int)c->h_subs.size();
+        for (int z = 0; z < hs.n[2]; z += tz)
+          for (int y = 0; y < hs.n[1]; y += ty)
+            for (int x = 0; x < hs.n[0]; x += tx) wl.push_back(WorkItem{sidx, x, y, z});
+      }
+      sd.tile_end = (int)wl.size();
+      c->h_subs.push_back(sd);
+    }
+    pd.tile_end = (int)wl.size();
+    if (live) c->live_tiles += pd.tile_end - pd.tile_begin;
+  }
+  pma_status st;
+  if ((st = ensure_buf(&c->d_subs, &c->subs_cap, c->h_subs.size() + 1)) != PMA_OK) return st;
+  if (!c->h_subs.empty())
+    PMA_CK(cudaMemcpyAsync(c->d_subs, c->h_subs.data(), sizeof(SubDesc) * c->h_subs.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+  for (int k = 0; k < NUM_CLS; ++k) {
+    const size_t cap = c->work_cap[k];
+    if ((st = ensure_buf(&c->d_work[k], &c->work_cap[k], c->h_work[k].size() + 1)) != PMA_OK)
+      return st;
+    if (c->work_cap[k] != cap || !c->d_part[k]) {
+      if (c->d_part[k]) cudaFree(c->d_part[k]);
+      c->d_part[k] = nullptr;
+      PMA_CK(cudaMalloc(&c->d_part[k], sizeof(Partial) * c->work_cap[k]));
+    }
+    c->nwork[k] = (int)c->h_work[k].size();
+    if (c->nwork[k])
+      PMA_CK(cudaMemcpyAsync(c->d_work[k], c->h_work[k].data(),
+                             sizeof(WorkItem) * c->nwork[k], cudaMemcpyHostToDevice,
+                             c->stream));
+    const int per_sm = sweep_max_blocks_per_sm(k, c->tile_id[k]);
+    c->grid[k] = std::min(c->nwork[k], per_sm * c->num_sms);
+  }
+  PMA_CK(cudaMemcpyAsync(c->d_probs, c->h_probs.data(), sizeof(ProbDesc) * c->slot_cap,
+                         cudaMemcpyHostToDevice, c->stream));
+  // The host-side vectors must stay alive until the copies complete.
+  PMA_CK(cudaStreamSynchronize(c->stream));
+  c->dirty = false;
+  c->graph_valid = false;
+  return PMA_OK;
+}
+
+LaunchArgs args_for(pma_ctx* c, int k, int t0, int n) {
+  LaunchArgs a;
+  a.work = c->d_work[k];
+  a.t0 = t0;
+  a.nwork = n;
+  a.subs = c->d_subs;
+  a.probs = c->d_probs;
+  a.st = c->d_state;
+  a.part = c->d_part[k];
+  a.grid = std::min(n, c->grid[k] > 0 ? c->grid[k] : n);
+  return a;
+}
+
+pma_status launch_step(pma_ctx* c) {
+  for (int k = 0; k < NUM_CLS; ++k) {
+    if (c->nwork[k] == 0) continue;
+    if (c->launch_mode == PMA_LAUNCH_PER_SUBDOMAIN) {
+      for (const SubDesc& sd : c->h_subs) {
+        const int n = sd.tile_end - sd.tile_begin;
+        if (n <= 0 || c->h_probs[sd.prob].cls != k) continue;
+        LaunchArgs a = args_for(c, k, sd.tile_begin, n);
+        PMA_CK(launch_sweep(k, c->tile_id[k], a, c->stream));
+      }
+    } else {
+      LaunchArgs a = args_for(c, k, 0, c->nwork[k]);
+      PMA_CK(launch_sweep(k, c->tile_id[k], a, c->stream));
+    }
+  }
+  return PMA_OK;
+}
+
+pma_status run_window(pma_ctx* c, int steps) {
+  if (c->dirty) {
+    pma_status st = rebuild(c);
+    if (st != PMA_OK) return st;
+  }
+  const bool graphs = c->use_graphs && c->launch_mode == PMA_LAUNCH_BATCHED;
+  if (graphs) {
+    if (!c->graph_valid || c->graph_steps != steps) {
+      if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      PMA_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      pma_status st = PMA_OK;
+      for (int s = 0; s < steps && st == PMA_OK; ++s) st = launch_step(c);
+      cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+      if (st != PMA_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      PMA_CK(ce);
+      cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
+      cudaGraphDestroy(g);
+      PMA_CK(ie);
+      c->graph_steps = steps;
+      c->graph_valid = true;
+    }
+    PMA_CK(cudaGraphLaunch(c->gexec, c->stream));
+  } else {
+    for (int s = 0; s < steps; ++s) {
+      pma_status st = launch_step(c);
+      if (st != PMA_OK) return st;
+    }
+  }
+  PMA_CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(ProbState) * c->slot_cap,
+                         cudaMemcpyDeviceToHost, c->stream));
+  PMA_CK(cudaStreamSynchronize(c->stream));
+  return PMA_OK;
+}
+
+// Retire finished requests (lock held).
+void collect(pma_ctx* c) {
+  std::vector<uint64_t> still;
+  const auto now = Clock::now();
+  for (uint64_t id : c->active) {
+    Request& r = *c->reqs[id];
+    const ProbState& ps = c->h_state[r.slot];
+    if (ps.phase == PH_DONE) {
+      r.state = RQ_FINISHED;
+      r.t_done = now;
+      r.info.steps = ps.step;
+      r.info.residual = ps.residual;
+      r.info.theta = ps.theta;
+      r.info.min_det = ps.min_det;
+      r.info.shift = ps.shift;
+      r.info.status = ps.status;
+      r.info.latency_us =
+          std::chrono::duration<double, std::micro>(r.t_done - r.t_submit).count();
+    } else {
+      still.push_back(id);
+    }
+  }
+  if (still.size() != c->active.size()) {
+    // compact the work lists when most tiles belong to finished requests
+    long long live = 0;
+    for (uint64_t id : still) {
+      const Request& r = *c->reqs[id];
+      const ProbDesc& pd = c->h_probs[r.slot];
+      live += pd.tile_end - pd.tile_begin;
+    }
+    if (live * 2 < c->live_tiles) c->dirty = true;
+    c->active.swap(still);
+    c->cv.notify_all();
+  }
+}
+
+// Admit queued requests while memory and slots allow (lock held).
+pma_status admit(pma_ctx* c) {
+  while (!c->queue.empty()) {
+    if (c->max_active > 0 && (int)c->active.size() >= c->max_active) break;
+    Request& r = *c->reqs[c->queue.front()];
+    if (c->budget && c->used + r.bytes > c->budget) break;
+    pma_status st = ensure_slots(c, (int)(c->slot_cap - c->free_slots.size()) + 1);
+    if (st != PMA_OK) return st;
+    void* blk = nullptr;
+    cudaError_t e = cudaMallocAsync(&blk, r.bytes, c->stream);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      if (c->active.empty()) {
+        set_err(std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+        return PMA_ERR_NOMEM;
+      }
+      break;  // wait for memory to free up
+    }
+    r.block = (char*)blk;
+    c->used += r.bytes;
+    if (!r.psi0.empty())
+      PMA_CK(cudaMemcpyAsync(r.block + r.psi_off, r.psi0.data(), sizeof(double) * r.nodes,
+                             cudaMemcpyHostToDevice, c->stream));
+    r.slot = c->free_slots.back();
+    c->free_slots.pop_back();
+    ProbState ps{};
+    ps.phase = PH_INIT_V;
+    ps.status = PMA_PENDING;
+    PMA_CK(cudaMemcpyAsync(c->d_state + r.slot, &ps, sizeof(ps), cudaMemcpyHostToDevice,
+                           c->stream));
+    PMA_CK(cudaStreamSynchronize(c->stream));
+    c->h_state[r.slot] = ps;
+    r.state = RQ_ACTIVE;
+    c->active.push_back(r.id);
+    c->queue.pop_front();
+    c->dirty = true;
+  }
+  return PMA_OK;
+}
+
+void free_request(pma_ctx* c, Request& r) {
+  if (r.block) {
+    cudaFreeAsync(r.block, c->stream);
+    r.block = nullptr;
+    c->used -= r.bytes;
+  }
+  if (r.slot >= 0) {
+    c->free_slots.push_back(r.slot);
+    r.slot = -1;
+  }
+  // A freed slot is only reused through admit(), which rebuilds the tables
+  // before the next window, so finished requests need no rebuild here.
+}
+
+pma_status ensure_jobs(pma_ctx* c, int n) {
+  if (n <= c->jobs_cap) return PMA_OK;
+  if (c->d_jobs) cudaFree(c->d_jobs);
+  c->d_jobs = nullptr;
+  PMA_CK(cudaMalloc(&c->d_jobs, sizeof(CombineJob) * n));
+  c->jobs_cap = n;
+  return PMA_OK;
+}
+
+// Combine one finished request into device buffers (lock held).
+pma_status combine_into(pma_ctx* c, Request& r, void* x, int out_fp64, void* psi) {
+  if (c->dirty) {
+    pma_status st = rebuild(c);
+    if (st != PMA_OK) return st;
+  }
+  pma_status st = ensure_jobs(c, 1);
+  if (st != PMA_OK) return st;
+  CombineJob j{r.slot, out_fp64, x, psi};
+  PMA_CK(cudaMemcpyAsync(c->d_jobs, &j, sizeof(j), cudaMemcpyHostToDevice, c->stream));
+  PMA_CK(launch_combine(c->d_jobs, 1, r.nodes, c->d_subs, c->d_probs, c->d_state, c->stream));
+  return PMA_OK;
+}
+
+pma_status loop_once(pma_ctx* c, std::unique_lock<std::mutex>& lk, bool* idle) {
+  pma_status st = admit(c);
+  if (st != PMA_OK) return st;
+  *idle = c->active.empty();
+  if (*idle) return PMA_OK;
+  st = run_window(c, c->window);
+  if (st != PMA_OK) return st;
+  collect(c);
+  (void)lk;
+  return PMA_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+extern "C" {
+
+const char* pma_status_str(int32_t s) {
+  switch (s) {
+    case PMA_OK: return "ok";
+    case PMA_NOT_CONVERGED: return "not converged";
+    case PMA_PENDING: return "pending";
+    case PMA_ERR_INVALID: return "invalid argument";
+    case PMA_ERR_NOMEM: return "out of device memory";
+    case PMA_ERR_TANGLED: return "mesh tangled";
+    case PMA_ERR_TIMEOUT: return "timeout";
+    case PMA_ERR_CUDA: return "CUDA error";
+    case PMA_ERR_BUSY: return "busy";
+    case PMA_ERR_NOT_FOUND: return "unknown request";
+  }
+  return "unknown status";
+}
+
+const char* pma_last_error(void) { return g_err.c_str(); }
+
+int32_t pma_abi_version(void) { return PMA_ABI_VERSION; }
+
+pma_status pma_create(pma_ctx** out, int device, size_t mem_budget_bytes, void* stream) {
+  if (!out) return PMA_ERR_INVALID;
+  *out = nullptr;
+  std::unique_ptr<pma_ctx> c(new pma_ctx());
+  c->device = device;
+  PMA_CK(cudaSetDevice(device));
+  PMA_CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    PMA_CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  c->budget = mem_budget_bytes;
+  pma_status st = ensure_slots(c.get(), 64);
+  if (st != PMA_OK) return st;
+  PMA_CK(cudaMalloc(&c->d_check, sizeof(double) * 4 + sizeof(unsigned long long)));
+  *out = c.release();
+  return PMA_OK;
+}
+
+pma_status pma_destroy(pma_ctx* c) {
+  if (!c) return PMA_ERR_INVALID;
+  pma_serve_stop(c);
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->reqs)
+    if (kv.second->block) cudaFreeAsync(kv.second->block, c->stream);
+  cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  cudaFree(c->d_probs);
+  cudaFree(c->d_state);
+  cudaFreeHost(c->h_state);
+  cudaFree(c->d_subs);
+  for (int k = 0; k < NUM_CLS; ++k) {
+    cudaFree(c->d_work[k]);
+    cudaFree(c->d_part[k]);
+  }
+  cudaFree(c->d_jobs);
+  cudaFree(c->d_check);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return PMA_OK;
+}
+
+pma_status pma_set_option(pma_ctx* c, int32_t opt, int64_t v) {
+  if (!c) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  switch (opt) {
+    case PMA_OPT_WINDOW_STEPS:
+      if (v < 1 || v > 100000) return PMA_ERR_INVALID;
+      c->window = (int)v;
+      break;
+    case PMA_OPT_USE_GRAPHS: c->use_graphs = v ? 1 : 0; break;
+    case PMA_OPT_LAUNCH_MODE:
+      if (v != PMA_LAUNCH_BATCHED && v != PMA_LAUNCH_PER_SUBDOMAIN) return PMA_ERR_INVALID;
+      c->launch_mode = (int)v;
+      break;
+    case PMA_OPT_TILE_2D:
+      if (v < 0 || v >= tile2d_count()) return PMA_ERR_INVALID;
+      c->opt_tile2d = (int)v;
+      c->dirty = true;
+      break;
+    case PMA_OPT_TILE_3D:
+      if (v < 0 || v >= tile3d_count()) return PMA_ERR_INVALID;
+      c->opt_tile3d = (int)v;
+      c->dirty = true;
+      break;
+    case PMA_OPT_MAX_ACTIVE:
+      if (v < 0) return PMA_ERR_INVALID;
+      c->max_active = (int)v;
+      break;
+    default: return PMA_ERR_INVALID;
+  }
+  c->graph_valid = false;
+  return PMA_OK;
+}
+
+pma_status pma_get_option(pma_ctx* c, int32_t opt, int64_t* v) {
+  if (!c || !v) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  switch (opt) {
+    case PMA_OPT_WINDOW_STEPS: *v = c->window; break;
+    case PMA_OPT_USE_GRAPHS: *v = c->use_graphs; break;
+    case PMA_OPT_LAUNCH_MODE: *v = c->launch_mode; break;
+    case PMA_OPT_TILE_2D: *v = c->opt_tile2d; break;
+    case PMA_OPT_TILE_3D: *v = c->opt_tile3d; break;
+    case PMA_OPT_MAX_ACTIVE: *v = c->max_active; break;
+    default: return PMA_ERR_INVALID;
+  }
+  return PMA_OK;
+}
+
+pma_status pma_submit(pma_ctx* c, const pma_grid* grid, const pma_monitor* mon,
+                      const pma_decomp* dec, const pma_params* par, const double* psi0,
+                      uint64_t* req_id) {
+  if (!c || !grid || !mon || !par || !req_id) return PMA_ERR_INVALID;
+  std::unique_ptr<Request> r(new Request());
+  r->g = *grid;
+  r->m = *mon;
+  if (dec) {
+    r->d = *dec;
+  } else {
+    r->d.parts[0] = r->d.parts[1] = r->d.parts[2] = 1;
+    r->d.overlap = 0;
+    r->d.transmission = PMA_TRANSMISSION_PARALLEL;
+  }
+  r->p = *par;
+  if (psi0) {
+    long long n = 1;
+    for (int a = 0; a < grid->dim && a < 3; ++a) n *= grid->n[a] > 0 ? grid->n[a] : 0;
+    if (n <= 0) return PMA_ERR_INVALID;
+    r->psi0.assign(psi0, psi0 + n);
+  }
+  pma_status st = build_request(*r);
+  if (st != PMA_OK) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->budget && r->bytes > c->budget) {
+    set_err("request larger than the memory budget");
+    return PMA_ERR_NOMEM;
+  }
+  r->id = c->next_id++;
+  r->t_submit = Clock::now();
+  r->info.status = PMA_PENDING;
+  *req_id = r->id;
+  c->queue.push_back(r->id);
+  c->reqs[r->id] = std::move(r);
+  c->cv.notify_all();
+  return PMA_OK;
+}
+
+pma_status pma_run(pma_ctx* c, int64_t max_windows, int32_t* n_active) {
+  if (!c) return PMA_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(c->mu);
+  if (c->serving) return PMA_ERR_BUSY;
+  PMA_CK(cudaSetDevice(c->device));
+  int64_t w = 0;
+  pma_status st = PMA_OK;
+  while (max_windows <= 0 || w < max_windows) {
+    bool idle = false;
+    st = loop_once(c, lk, &idle);
+    if (st != PMA_OK) break;
+    if (idle) {
+      if (c->queue.empty()) break;
+      // a queued request that cannot be admitted with nothing active
+      set_err("queued request cannot be admitted");
+      st = PMA_ERR_NOMEM;
+      break;
+    }
+    ++w;
+  }
+  if (n_active) *n_active = (int32_t)(c->active.size() + c->queue.size());
+  return st;
+}
+
+static void server_main(pma_ctx* c) {
+  cudaSetDevice(c->device);
+  std::unique_lock<std::mutex> lk(c->mu);
+  while (!c->stop.load()) {
+    bool idle = false;
+    pma_status st = loop_once(c, lk, &idle);
+    if (st != PMA_OK) {
+      c->server_err = st;
+      // fail every pending request so that waiters return
+      for (auto& kv : c->reqs)
+        if (kv.second->state != RQ_FINISHED) {
+          kv.second->state = RQ_FINISHED;
+          kv.second->info.status = st;
+        }
+      c->active.clear();
+      c->queue.clear();
+      c->cv.notify_all();
+      break;
+    }
+    if (idle) c->cv.wait_for(lk, std::chrono::microseconds(200));
+  }
+}
+
+pma_status pma_serve_start(pma_ctx* c) {
+  if (!c) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->serving) return PMA_ERR_BUSY;
+  c->stop = false;
+  c->serving = true;
+  c->server = std::thread(server_main, c);
+  return PMA_OK;
+}
+
+pma_status pma_serve_stop(pma_ctx* c) {
+  if (!c) return PMA_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->serving) return PMA_OK;
+    c->stop = true;
+    c->cv.notify_all();
+  }
+  if (c->server.joinable()) c->server.join();
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->serving = false;
+  return c->server_err;
+}
+
+pma_status pma_poll(pma_ctx* c, uint64_t id, int32_t* done) {
+  if (!c || !done) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->reqs.find(id);
+  if (it == c->reqs.end()) return PMA_ERR_NOT_FOUND;
+  *done = it->second->state == RQ_FINISHED ? 1 : 0;
+  return PMA_OK;
+}
+
+pma_status pma_wait(pma_ctx* c, uint64_t id, int64_t timeout_us) {
+  if (!c) return PMA_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(c->mu);
+  auto deadline = Clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
+  for (;;) {
+    auto it = c->reqs.find(id);
+    if (it == c->reqs.end()) return PMA_ERR_NOT_FOUND;
+    if (it->second->state == RQ_FINISHED) return (pma_status)it->second->info.status;
+    if (!c->serving) {
+      // drive the work on this thread
+      lk.unlock();
+      int32_t n = 0;
+      pma_status st = pma_run(c, 1, &n);
+      lk.lock();
+      if (st != PMA_OK) return st;
+      continue;
+    }
+    if (timeout_us < 0) {
+      c->cv.wait(lk);
+    } else if (c->cv.wait_until(lk, deadline) == std::cv_status::timeout) {
+      auto it2 = c->reqs.find(id);
+      if (it2 != c->reqs.end() && it2->second->state == RQ_FINISHED)
+        return (pma_status)it2->second->info.status;
+      return PMA_ERR_TIMEOUT;
+    }
+  }
+}
+
+pma_status pma_get_mesh_device(pma_ctx* c, uint64_t id, void* x_dev, int32_t out_fp64,
+                               void* psi_dev, pma_info* info) {
+  if (!c || !x_dev) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->reqs.find(id);
+  if (it == c->reqs.end()) return PMA_ERR_NOT_FOUND;
+  Request& r = *it->second;
+  if (r.state != RQ_FINISHED) return PMA_ERR_BUSY;
+  if (!r.block) return (pma_status)r.info.status;
+  PMA_CK(cudaSetDevice(c->device));
+  pma_status st = combine_into(c, r, x_dev, out_fp64 ? 1 : 0, psi_dev);
+  if (st != PMA_OK) return st;
+  if (info) *info = r.info;
+  return (pma_status)r.info.status;
+}
+
+pma_status pma_get_mesh(pma_ctx* c, uint64_t id, double* x_out, double* psi_out,
+                        pma_info* info) {
+  if (!c || !x_out) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->reqs.find(id);
+  if (it == c->reqs.end()) return PMA_ERR_NOT_FOUND;
+  Request& r = *it->second;
+  if (r.state != RQ_FINISHED) return PMA_ERR_BUSY;
+  if (!r.block) return (pma_status)r.info.status;
+  PMA_CK(cudaSetDevice(c->device));
+  const size_t nx = (size_t)r.dim * r.nodes, np = psi_out ? (size_t)r.nodes : 0;
+  double* tmp = nullptr;
+  PMA_CK(cudaMallocAsync(&tmp, sizeof(double) * (nx + np), c->stream));
+  pma_status st = combine_into(c, r, tmp, 1, psi_out ? tmp + nx : nullptr);
+  if (st == PMA_OK) {
+    cudaError_t e = cudaMemcpyAsync(x_out, tmp, sizeof(double) * nx, cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e == cudaSuccess && psi_out)
+      e = cudaMemcpyAsync(psi_out, tmp + nx, sizeof(double) * np, cudaMemcpyDeviceToHost,
+                          c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      set_err(std::string("mesh copy: ") + cudaGetErrorString(e));
+      st = PMA_ERR_CUDA;
+    }
+  }
+  cudaFreeAsync(tmp, c->stream);
+  if (st != PMA_OK) return st;
+  if (info) *info = r.info;
+  pma_status fin = (pma_status)r.info.status;
+  free_request(c, r);
+  c->reqs.erase(it);
+  return fin;
+}
+
+pma_status pma_check_mesh(pma_ctx* c, uint64_t id, double* out4) {
+  if (!c || !out4) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->reqs.find(id);
+  if (it == c->reqs.end()) return PMA_ERR_NOT_FOUND;
+  Request& r = *it->second;
+  if (r.state != RQ_FINISHED || !r.block) return PMA_ERR_BUSY;
+  PMA_CK(cudaSetDevice(c->device));
+  if (c->dirty) {
+    pma_status st = rebuild(c);
+    if (st != PMA_OK) return st;
+  }
+  double init[4] = {INFINITY, INFINITY, INFINITY, 0.0};
+  PMA_CK(cudaMemcpyAsync(c->d_check, init, sizeof(double) * 3, cudaMemcpyHostToDevice,
+                         c->stream));
+  unsigned long long* cnt = (unsigned long long*)(c->d_check + 3);
+  PMA_CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), c->stream));
+  PMA_CK(launch_check(r.slot, r.nodes, c->d_subs, c->d_probs, c->d_state, c->d_check, cnt,
+                      c->stream));
+  double res[3];
+  unsigned long long n = 0;
+  PMA_CK(cudaMemcpyAsync(res, c->d_check, sizeof(double) * 3, cudaMemcpyDeviceToHost,
+                         c->stream));
+  PMA_CK(cudaMemcpyAsync(&n, cnt, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+  PMA_CK(cudaStreamSynchronize(c->stream));
+  out4[0] = res[0];
+  out4[1] = res[1];
+  out4[2] = res[2];
+  out4[3] = (double)n;
+  return PMA_OK;
+}
+
+pma_status pma_release(pma_ctx* c, uint64_t id) {
+  if (!c) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->reqs.find(id);
+  if (it == c->reqs.end()) return PMA_ERR_NOT_FOUND;
+  Request& r = *it->second;
+  if (r.state == RQ_ACTIVE) {
+    // its tiles are in the work lists: drop them before the next window
+    cudaStreamSynchronize(c->stream);
+    c->active.erase(std::remove(c->active.begin(), c->active.end(), id), c->active.end());
+    c->dirty = true;
+  } else if (r.state == RQ_QUEUED) {
+    c->queue.erase(std::remove(c->queue.begin(), c->queue.end(), id), c->queue.end());
+  }
+  free_request(c, r);
+  c->reqs.erase(it);
+  return PMA_OK;
+}
+
+pma_status pma_counts(pma_ctx* c, int32_t* queued, int32_t* active, int32_t* finished) {
+  if (!c) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  int f = 0;
+  for (auto& kv : c->reqs)
+    if (kv.second->state == RQ_FINISHED) ++f;
+  if (queued) *queued = (int32_t)c->queue.size();
+  if (active) *active = (int32_t)c->active.size();
+  if (finished) *finished = f;
+  return PMA_OK;
+}
+
+pma_status pma_solve(int device, const pma_grid* grid, const pma_monitor* mon,
+                     const pma_decomp* dec, const pma_params* par, const double* psi0,
+                     double* x_out, double* psi_out, pma_info* info) {
+  pma_ctx* c = nullptr;
+  pma_status st = pma_create(&c, device, 0, nullptr);
+  if (st != PMA_OK) return st;
+  uint64_t id = 0;
+  st = pma_submit(c, grid, mon, dec, par, psi0, &id);
+  if (st == PMA_OK) {
+    int32_t n = 0;
+    st = pma_run(c, 0, &n);
+    if (st == PMA_OK) st = pma_get_mesh(c, id, x_out, psi_out, info);
+  }
+  pma_destroy(c);
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+// pma_internal.h -- device-side tables shared by the sm_103a kernels and the
+// host runtime of the DDPMA library.  Not part of the public ABI.
+//
+// Data layout in HBM (one request = one "problem"):
+//   * every subdomain owns two contiguous state buffers v[0], v[1] (ping-pong)
+//     of n0*n1*n2 values of the deviation potential v = Psi - |xi|^2/2,
+//     x fastest; FP32 or FP64 per request;
+//   * the per-step sweep reads v[parity] and writes v[parity^1];
+//   * per-tile partial reductions (one 64-byte record per tile) are folded
+//     into per-problem scalars by the last tile of each problem;
+//   * per-problem scalars (step, normalisation, shift, status) live in a
+//     device array indexed by a stable slot number.
+#pragma once
+
+#include <cstdint>
+
+#include "pma.h"
+
+namespace pma {
+
+constexpr int kMaxParts = PMA_MAX_PARTS;
+constexpr int kMaxTerms = PMA_MAX_TERMS;
+
+// Kernel classes: one work list and one launch per class and step.
+enum Cls : int { CLS_2D_F32 = 0, CLS_2D_F64 = 1, CLS_3D_F32 = 2, CLS_3D_F64 = 3, NUM_CLS = 4 };
+
+// Phases of a problem on the device.
+enum Phase : int {
+  PH_INIT_V = 0,      // next launch writes v^0 (Eq. incond or warm start)
+  PH_INIT_THETA = 1,  // next launch computes theta^0 only (no update)
+  PH_RUN = 2,         // forward-Euler steps
+  PH_DONE = 3
+};
+
+struct MonDev {
+  int kind, nterms;
+  double base, p0;
+  pma_term t[kMaxTerms];
+};
+
+struct ProbDesc {
+  int dim;
+  int N[3];
+  double lo[3];
+  double h[3];
+  double vol;
+  int parts[3];
+  int bcore[3][kMaxParts + 1];  // core boundaries b_k per axis
+  int sub_base;                 // first subdomain in the subdomain table
+  int nsub;
+  int tile_begin, tile_end;     // range in this problem's class work list
+  int cls;
+  int stop_norm, stop_rule, check_every, rhs, normalize, transmission;
+  int pad0;
+  double dt, tol;
+  long long max_steps;
+  const double* psi0;           // optional warm start (global grid), device
+  MonDev mon;
+};
+
+struct SubDesc {
+  int prob;          // problem slot
+  int n[3];          // local node counts (1 on unused axes)
+  int g0[3];         // global index of local node 0
+  int clo[3], chi[3];// owned core, local indices, inclusive
+  int k[3];          // block index per axis
+  int faces;         // bit 2a: low face of axis a is physical; bit 2a+1: high
+  int idx;           // subdomain index within its problem (raster order)
+  int tile_begin, tile_end;  // its tiles in the class work list
+  int pad;
+  void* v[2];        // ping-pong state buffers
+};
+
+struct ProbState {
+  long long step;       // forward-Euler steps taken
+  int phase;            // Phase
+  int status;           // pma_status once done
+  int parity;           // buffer holding v^step
+  unsigned int tiles_done;  // arrival counter of the current launch
+  double c_lag;         // normalisation constant used by the next update
+  double corr;          // shift of transmission nodes relative to the rest
+  double shift;         // S: v_device = v_exact + S at updated nodes
+  double theta;         // theta of the last evaluated step
+  double theta_prev;    // theta used by the root form (previous step)
+  double residual;
+  double min_det;
+  double pad;
+};
+
+struct WorkItem {
+  int sub;
+  int x0, y0, z0;
+};
+
+struct Partial {
+  double theta;   // sum of w rho det over owned nodes
+  double l2a;     // sum of w (G - c_lag)^2 over updated nodes (local trapezoid)
+  double l2b;     // sum of w (G - c_lag)
+  double wsum;    // sum of w
+  double gmax, gmin, dmin;
+  int nonfinite;
+  int sub;
+};
+
+static_assert(sizeof(Partial) == 64, "partial record is one 64-byte line");
+static_assert(sizeof(WorkItem) == 16, "work item is 16 bytes");
+
+// Tile shapes (nodes per CTA).  2D: TX x TY, one node per thread and RY rows
+// per thread; 3D: TX x TY threads marching TZ planes.
+struct Tile2D { int tx, ty; };
+struct Tile3D { int tx, ty, tz; };
+
+// Kernel launch entry points (pma_kernels.cu).
+struct LaunchArgs {
+  const WorkItem* work;  // class work list (absolute base)
+  int t0;                // first work item of this launch
+  int nwork;             // work items of this launch
+  const SubDesc* subs;
+  const ProbDesc* probs;
+  ProbState* st;
+  Partial* part;
+  int grid;   // CTAs (grid-stride over the work list)
+};
+
+int tile2d_count();
+int tile3d_count();
+Tile2D tile2d_shape(int id);
+Tile3D tile3d_shape(int id);
+
+// cls selects dim/precision; tile_id a compiled tile shape.
+cudaError_t launch_sweep(int cls, int tile_id, const LaunchArgs& a, cudaStream_t s);
+int sweep_max_blocks_per_sm(int cls, int tile_id);
+
+struct CombineJob {
+  int prob;        // slot
+  int out_fp64;
+  void* x;         // dim * N values
+  void* psi;       // optional N values
+};
+cudaError_t launch_combine(const CombineJob* jobs_dev, int njobs, long long max_nodes,
+                           const SubDesc* subs, const ProbDesc* probs, const ProbState* st,
+                           cudaStream_t s);
+
+// FP64 positivity check of one problem; out (device) receives 4 doubles.
+cudaError_t launch_check(int prob, long long nodes, const SubDesc* subs, const ProbDesc* probs,
+                         const ProbState* st, double* out, unsigned long long* cnt,
+                         cudaStream_t s);
+
+}  // namespace pma

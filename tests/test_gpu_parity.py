@@ -1,0 +1,207 @@
+"""Parity of the sm_103a path (through the C ABI) with the FP64 oracle.
+
+FP64 device runs must match node positions within 1e-11 (times the domain
+size); FP32 runs within 1e-5, after the same number of steps.  Step counts,
+statuses and the stop decision must agree exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_14602_gb300 import pma
+from paper_2006_14602_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2006_14602_gb300 import build
+    build.build()
+    pma.load()
+
+
+def _size(prob):
+    return max(prob.hi[a] - prob.lo[a] for a in range(prob.dim))
+
+
+def _check(prob, ref=None, tol=None, psi=True, **opts):
+    if ref is None:
+        ref = oracle.solve(prob)
+    x, p, info = pma.solve(prob, want_psi=psi, **opts)
+    if tol is None:
+        tol = TOL64 if prob.precision == "fp64" else TOL32
+    assert info.steps == ref.steps, (info.steps, ref.steps)
+    assert pma.STATUS_NAMES[info.status] == ref.status
+    err = np.abs(x - ref.x).max() / _size(prob)
+    assert err <= tol, err
+    if psi and prob.precision == "fp64":
+        assert np.abs(p - ref.psi).max() <= 1e3 * tol, np.abs(p - ref.psi).max()
+    return x, p, info, ref, err
+
+
+# ------------------------------------------------------------------ 2D
+
+def test_config1_fp64():
+    """33^2 ring, dt = 1e-4, 2000-step cap (not converged at the cap)."""
+    prob = W.config1()
+    x, p, info, ref, err = _check(prob)
+    assert info.status == pma.PMA_NOT_CONVERGED
+    assert abs(info.residual - ref.residual) <= 1e-9 * ref.residual
+
+
+def test_config1_uncapped_converges_at_same_step():
+    prob = W.config1().replace(max_steps=6000)
+    x, p, info, ref, err = _check(prob)
+    assert info.status == pma.PMA_OK and info.steps == ref.steps == 2857
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,parts,o", [((45, 37), (3, 2), 5), ((70, 33), (1, 3), 4),
+                                       ((21, 64), (2, 1), 2), ((97, 65), (4, 3), 8)])
+def test_dd_2d_ragged(prec, n, parts, o):
+    prob = W.Problem(dim=2, n=(n[0], n[1], 1), monitor=W.ring_monitor(), parts=(parts[0], parts[1], 1),
+                     overlap=o, dt=W.dt_for((n[0], n[1], 1), 2), tol=0.0, max_steps=150,
+                     precision=prec)
+    _check(prob)
+
+
+@pytest.mark.parametrize("mon", ["sine", "bumps", "product", "burgers"])
+def test_monitor_kinds_2d(mon):
+    rng = np.random.default_rng(5)
+    m = {"sine": W.sine_monitor(), "bumps": W.random_bumps(rng, 2, 4),
+         "product": W.product_monitor([(4.0, 40.0, 0.3), (2.0, 20.0, 0.6)]),
+         "burgers": W.Monitor("arclen_burgers", 1.0, [], p0=0.05)}[mon]
+    prob = W.Problem(dim=2, n=(41, 39, 1), monitor=m, parts=(2, 2, 1), overlap=4,
+                     dt=W.dt_for((41, 39, 1), 2, cfl=0.03), tol=0.0, max_steps=100,
+                     precision="fp64")
+    _check(prob)
+
+
+def test_spiral_monitor_short():
+    prob = W.Problem(dim=2, n=(33, 33, 1), monitor=W.Monitor("arclen_spiral", 1.0, []),
+                     dt=W.dt_for((33, 33, 1), 2, cfl=0.001), tol=0.0, max_steps=20,
+                     precision="fp64")
+    _check(prob)
+
+
+@pytest.mark.parametrize("variant", ["l2", "any", "check7", "none", "root"])
+def test_stop_rules_and_variants(variant):
+    base = W.Problem(dim=2, n=(29, 29, 1), monitor=W.ring_monitor(), parts=(2, 2, 1), overlap=4,
+                     dt=W.dt_for((29, 29, 1), 2), tol=2e-4, max_steps=3000, precision="fp64")
+    prob = {"l2": base.replace(stop_norm="l2_increment", tol=1e-9),
+            "any": base.replace(stop_rule="any"),
+            "check7": base.replace(check_every=7),
+            "none": base.replace(normalize="none", tol=0.0, max_steps=200),
+            "root": base.replace(rhs="root", lag_theta=1)}[variant]
+    x, p, info, ref, err = _check(prob)
+    if variant != "none":
+        assert info.status == pma.PMA_OK
+    assert abs(info.residual - ref.residual) <= 1e-8 * max(ref.residual, 1e-300)
+
+
+def test_warm_start():
+    prob = W.config1().replace(max_steps=300)
+    first = oracle.solve(prob)
+    ref = oracle.solve(prob, psi0=first.psi)
+    x, p, info = pma.solve(prob, psi0=first.psi)
+    assert info.steps == ref.steps
+    assert np.abs(x - ref.x).max() <= TOL64
+
+
+def test_tangle_is_reported_with_last_valid_mesh():
+    prob = W.small_case(2, 25, parts=(2, 2, 1), overlap=4, steps=400).replace(
+        dt=W.dt_for((25, 25, 1), 2, cfl=4.0))
+    ref = oracle.solve(prob)
+    assert ref.status == "tangled"
+    x, p, info = pma.solve(prob)
+    assert info.status == pma.PMA_ERR_TANGLED and info.steps == ref.steps
+    assert np.abs(x - ref.x).max() <= 1e-9
+    assert info.min_det <= 0 or not np.isfinite(info.min_det)
+
+
+def test_uniform_and_zero_steps():
+    prob = W.Problem(dim=2, n=(30, 30, 1), monitor=W.uniform_monitor(2.0), parts=(2, 2, 1),
+                     overlap=4, dt=1e-4, tol=0.0, max_steps=100, precision="fp32")
+    x, p, info = pma.solve(prob)
+    ident = np.stack(np.meshgrid(np.linspace(0, 1, 30), np.linspace(0, 1, 30), indexing="xy"))
+    assert np.abs(x - ident).max() < 1e-6
+    x, p, info = pma.solve(prob.replace(max_steps=0))
+    assert info.steps == 0 and info.status == pma.PMA_NOT_CONVERGED
+    assert np.abs(x - ident).max() == 0.0
+
+
+# ------------------------------------------------------------------ 3D
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,parts,o", [((19, 17, 15), (2, 2, 2), 4), ((26, 20, 35), (1, 2, 3), 5),
+                                       ((40, 9, 11), (3, 1, 1), 3)])
+def test_dd_3d(prec, n, parts, o):
+    prob = W.Problem(dim=3, n=n, monitor=W.shell_monitor(), parts=parts, overlap=o,
+                     dt=W.dt_for(n, 3, cfl=0.05), tol=0.0, max_steps=60, precision=prec)
+    _check(prob)
+
+
+@pytest.mark.parametrize("mon", ["tanh_sphere", "nine_spheres"])
+def test_monitor_kinds_3d(mon):
+    kind = "arclen_" + mon
+    lim = 1.0 if mon == "tanh_sphere" else 2.0
+    prob = W.Problem(dim=3, n=(17, 17, 17), lo=(-lim,) * 3, hi=(lim,) * 3,
+                     monitor=W.Monitor(kind, 1.0, []), parts=(2, 2, 2), overlap=4,
+                     dt=W.dt_for((17, 17, 17), 3, (-lim,) * 3, (lim,) * 3, cfl=0.002),
+                     tol=0.0, max_steps=15, precision="fp64")
+    _check(prob)
+
+
+# ------------------------------------------------------------------ modes
+
+def test_launch_modes_are_bitwise_identical():
+    prob = W.Problem(dim=2, n=(50, 44, 1), monitor=W.ring_monitor(), parts=(3, 2, 1), overlap=6,
+                     dt=W.dt_for((50, 44, 1), 2), tol=0.0, max_steps=77, precision="fp32")
+    a = pma.solve(prob, window_steps=32)[0]
+    b = pma.solve(prob, window_steps=5, use_graphs=0)[0]
+    c = pma.solve(prob, launch_mode=pma.PMA_LAUNCH_PER_SUBDOMAIN, window_steps=16)[0]
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    # another tile shape changes the summation order of theta (a uniform
+    # offset of v), so positions agree to rounding, not bitwise
+    ref = oracle.solve(prob)
+    for t in range(4):
+        d = pma.solve(prob, tile_2d=t)[0]
+        assert np.abs(d - a).max() < 1e-6 and np.abs(d - ref.x).max() < TOL32
+
+
+def test_alone_equals_in_mix():
+    """Each request's mesh is bitwise the same alone and in a batch."""
+    rng = np.random.default_rng(11)
+    probs = W.config4(seed=3, count=12, max_steps=120, size_range=(17, 90))
+    probs += [W.small_case(3, 15, parts=(2, 1, 2), overlap=4, steps=50, precision=p)
+              for p in ("fp32", "fp64")]
+    probs.append(W.config1().replace(max_steps=150))
+    mixed = pma.solve_many(probs)
+    for k in rng.choice(len(probs), size=6, replace=False):
+        alone = pma.solve(probs[k], want_psi=False)
+        assert np.array_equal(alone[0], mixed[k][0])
+        assert alone[2].steps == mixed[k][2].steps
+
+
+# ------------------------------------------------------------------ full sizes
+
+@pytest.mark.parametrize("mon", ["ring", "sine"])
+def test_config2_full_size(mon):
+    """257^2 in 4x4 subdomains (overlap 8), all 16 in one launch: FP64 within
+    1e-11 and FP32 within 1e-5 of the oracle after the same 300 steps."""
+    p64 = W.config2(mon, "fp64", max_steps=300)
+    ref = oracle.solve(p64)
+    _check(p64, ref)
+    _check(p64.replace(precision="fp32"), ref)
+
+
+def test_config3_full_size_fp32_vs_oracle():
+    """129^3 in 2x2x2 subdomains (overlap 6), FP32 sweep vs the FP64 oracle."""
+    prob = W.config3("fp32", max_steps=25)
+    _check(prob, psi=False)
