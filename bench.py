@@ -1,0 +1,480 @@
+#!/usr/bin/env python3
+"""Benchmark of the DDPMA mesh-generation hot path on GB300.
+
+One bench step = one pass of the whole hot path over one batch of seeded
+synthetic requests: admission tables in device memory, every forward-Euler
+step of every subdomain until each request meets its stop rule or its step
+cap, and the owner-takes combination of every request into its global mesh.
+
+  value      node-updates/s with the inputs resident in device memory,
+             device time from CUDA events on the library's stream;
+  e2e        the same through the public C API from host structs to host
+             meshes (host<->device copies inside the timed region);
+  roofline   the sweep kernel's algorithmic bytes (one read and one write of
+             v per node-update) over its event-timed windows, against the
+             measured HBM copy bandwidth;
+  cpu_baseline  the FP64 oracle on a bounded sample, on the host cores.
+
+Multi-GPU: the path does not exchange data between requests, so N GPUs run N
+independent replicas (weak scaling); value = all ranks' node-updates over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+from paper_2006_14602_gb300 import workloads as W
+
+METRIC = "PMA node-updates/s"
+UNIT = "node-updates/s"
+
+WORKLOADS = {
+    "c4": "uneven batch: 512 independent 2D problems, sides log-uniform in [17,513], "
+          "1-16 subdomains (overlap 4-8), 1-4 Gaussian bumps/rings, FP32, tol 1e-6 "
+          "or 2000 steps",
+    "c2": "2D 257x257 in 4x4 subdomains (overlap 8), ring and sine-wave monitors, FP32, "
+          "2000 steps, all 32 subdomains in one launch",
+    "c3": "3D 129^3 in 2x2x2 subdomains (overlap 6), spherical shell monitor, FP32 sweep, "
+          "FP64 residual/stop test, 2000 steps",
+}
+
+
+def make_workload(name: str, precision: str, max_steps=None):
+    if name == "c4":
+        probs = W.config4(precision=precision)
+    elif name == "c2":
+        probs = [W.config2("ring", precision), W.config2("sine", precision)]
+    elif name == "c3":
+        probs = [W.config3(precision)]
+    else:
+        raise SystemExit("unknown workload %s" % name)
+    if max_steps is not None:
+        probs = [p.replace(max_steps=max_steps) for p in probs]
+    return probs
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        med = statistics.median(sm) if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax or None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle leg
+def _oracle_job(args):
+    prob, = args
+    import oracle
+    t = time.perf_counter()
+    r = oracle.solve(prob)
+    dt = time.perf_counter() - t
+    nodes = _sub_nodes(prob)
+    return r.steps * nodes, dt
+
+
+def _sub_nodes(prob) -> int:
+    """Subdomain nodes of a problem (overlap duplicates counted), from the
+    decomposition rule of the input description."""
+    total = 1
+    for a in range(prob.dim):
+        n, p, o = prob.n[a], prob.parts[a], prob.overlap
+        if p == 1:
+            total *= n
+            continue
+        ol, oh = o // 2, o - o // 2
+        b = [(2 * k * n + p) // (2 * p) for k in range(p + 1)]
+        s = 0
+        for k in range(p):
+            lo = 0 if k == 0 else b[k] - ol
+            hi = n - 1 if k == p - 1 else b[k + 1] - 1 + oh
+            s += hi - lo + 1
+        total *= s
+    return total
+
+
+def oracle_sample(probs, budget_node_updates: float = 3.0e8, seed: int = 7):
+    """A bounded sample of the workload for the CPU oracle: a seeded subset
+    of requests with their step caps scaled so that the whole sample is about
+    budget_node_updates of work."""
+    import oracle  # noqa: F401  (build before forking workers)
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    idx = list(rng.permutation(len(probs)))
+    cores = max(1, min(os.cpu_count() or 1, 16))
+    pick = [probs[i] for i in idx[: max(cores, 1)]]
+    work = sum(_sub_nodes(p) * p.max_steps for p in pick)
+    scale = min(1.0, budget_node_updates / max(work, 1))
+    sample = [p.replace(max_steps=max(1, int(p.max_steps * scale)), tol=0.0,
+                        precision="fp64") for p in pick]
+    return sample, cores
+
+
+def run_oracle(sample, cores):
+    import multiprocessing as mp
+    t = time.perf_counter()
+    if cores > 1:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_oracle_job, [(p,) for p in sample])
+    else:
+        res = [_oracle_job((p,)) for p in sample]
+    wall = time.perf_counter() - t
+    nu = sum(r[0] for r in res)
+    return nu / wall, wall, nu
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    for f in ("pma_kernels.cu", "pma_device.cuh", "pma_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2006_14602_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(workload: str, precision: str):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "sweep_%s_%s.md" % (workload, precision))
+    if not os.path.exists(path):
+        return None, None
+    src = None
+    val = None
+    for line in open(path):
+        if line.startswith("kernel_source_sha1:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            try:
+                val = float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                val = None
+        if line.startswith("node_updates_per_launch:"):
+            pass
+    if src != kernel_source_hash():
+        return None, path
+    return val, path
+
+
+def percentile(xs, q):
+    if not xs:
+        return None
+    xs = sorted(xs)
+    k = (len(xs) - 1) * q
+    f, c = math.floor(k), math.ceil(k)
+    return xs[f] if f == c else xs[f] + (xs[c] - xs[f]) * (k - f)
+
+
+# ------------------------------------------------------------------ native arm
+def native(args, rank, world, device):
+    import torch
+    from paper_2006_14602_gb300 import build, pma
+
+    build.build()
+    pma.load()
+    torch.cuda.set_device(device)
+    stream = torch.cuda.Stream(device)
+    probs = make_workload(args.workload, args.precision, args.max_steps)
+    opts = {"window_steps": args.window}
+    if args.tile2d is not None:
+        opts["tile_2d"] = args.tile2d
+    if args.tile3d is not None:
+        opts["tile_3d"] = args.tile3d
+    ctx = pma.Context(device, 0, stream.cuda_stream, **opts)
+    nodes_out = [p.dim * p.nodes for p in probs]
+    out = torch.empty(sum(nodes_out), dtype=torch.float64, device=device)
+    offs = np.concatenate([[0], np.cumsum(nodes_out)])[:-1]
+    ptrs = [out.data_ptr() + 8 * int(o) for o in offs]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    host_out = torch.empty(sum(nodes_out), dtype=torch.float64, pin_memory=True)
+
+    def one_step(timed_events: bool):
+        ids = [ctx.submit(p) for p in probs]
+        st = pma.pma_admit(ctx.h)
+        if st != pma.PMA_OK:
+            raise pma.PmaError("pma_admit", st)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        pma.pma_get_stats(ctx.h, 1)
+        e0.record(stream)
+        ctx.run()
+        st = pma.pma_get_mesh_device_batch(ctx.h, ids, ptrs, 1)
+        if st != pma.PMA_OK:
+            raise pma.PmaError("pma_get_mesh_device_batch", st)
+        e1.record(stream)
+        e1.synchronize()
+        _, stats = pma.pma_get_stats(ctx.h, 1)
+        infos = []
+        for i in ids:
+            infos.append(_info(pma, ctx, i))
+            pma.pma_release(ctx.h, i)
+        return e0.elapsed_time(e1), stats, infos
+
+    def e2e_step():
+        # public API from host structs to host meshes, copies included
+        torch.cuda.synchronize(device)
+        pma.pma_get_stats(ctx.h, 1)
+        t0 = time.perf_counter()
+        ids = [ctx.submit(p) for p in probs]
+        ctx.run()
+        st = pma.pma_get_mesh_device_batch(ctx.h, ids, ptrs, 1)
+        if st != pma.PMA_OK:
+            raise pma.PmaError("pma_get_mesh_device_batch", st)
+        with torch.cuda.stream(stream):
+            host_out.copy_(out, non_blocking=True)
+        stream.synchronize()
+        t1 = time.perf_counter()
+        _, stats = pma.pma_get_stats(ctx.h, 1)
+        for i in ids:
+            pma.pma_release(ctx.h, i)
+        return (t1 - t0) * 1e3, stats
+
+    for _ in range(args.warmup):
+        one_step(False)
+    sampler = ClockSampler(device) if rank == 0 else None
+    _barrier(world, device)
+    if sampler:
+        sampler.start()
+    times, all_stats, lat = [], [], []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        _barrier(world, device)
+        torch.cuda.synchronize(device)
+        ms, stats, infos = one_step(True)
+        torch.cuda.synchronize(device)
+        times.append(ms)
+        all_stats.append(stats)
+        lat.extend(i["latency_ms"] for i in infos)
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop() if sampler else None
+    e2e_times, e2e_stats = [], []
+    for _ in range(max(1, min(args.steps, 3))):
+        ms, stats = e2e_step()
+        e2e_times.append(ms)
+        e2e_stats.append(stats)
+
+    node_updates = sum(s.node_updates for s in all_stats)
+    total_ms = sum(times)
+    sweep_ms = sum(s.window_ms for s in all_stats)
+    sweep_bytes = sum(s.sweep_bytes for s in all_stats)
+    launches = sum(s.sweep_launches for s in all_stats)
+    other = sum(s.other_launches for s in all_stats)
+    local = {
+        "node_updates": node_updates, "ms": total_ms, "sweep_ms": sweep_ms,
+        "sweep_bytes": sweep_bytes, "launches": launches + other, "sweep_launches": launches,
+        "e2e_ms": sum(e2e_times), "e2e_nu": sum(s.node_updates for s in e2e_stats),
+        "h2d": sum(s.h2d_bytes for s in e2e_stats) / len(e2e_stats),
+        "d2h": sum(s.d2h_bytes for s in e2e_stats) / len(e2e_stats) + host_out.numel() * 8,
+        "meshes": len(probs) * args.steps, "lat": lat, "wall_s": t_wall,
+        "infos_steps": [i["steps"] for i in infos],
+    }
+    agg = _gather(world, local, device)
+    ctx.close()
+    return agg, clocks, probs
+
+
+def _info(pma, ctx, rid):
+    st, info = pma.pma_get_info(ctx.h, rid)
+    if st != pma.PMA_OK:
+        raise pma.PmaError("pma_get_info", st)
+    return {"status": info.status, "steps": info.steps, "latency_ms": info.latency_us / 1e3}
+
+
+def _barrier(world, device):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier(device_ids=[device])
+
+
+def _gather(world, local, device):
+    if world == 1:
+        return [local]
+    import torch.distributed as dist
+    out = [None] * world
+    dist.all_gather_object(out, local)
+    return out
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--max-steps", type=int, default=None,
+                    help="override the per-request step cap (testing only)")
+    ap.add_argument("--window", type=int, default=64)
+    ap.add_argument("--tile2d", type=int, default=None, help="2D work shape id (default: auto)")
+    ap.add_argument("--tile3d", type=int, default=None, help="3D work shape id (default: auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return reference_arm(args, world)
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    # CPU baseline first (spawned workers, before the first GPU call)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        probs0 = make_workload(args.workload, args.precision, args.max_steps)
+        sample, cores = oracle_sample(probs0)
+        v, wall, nu = run_oracle(sample, cores)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d of the workload's requests (seeded), FP64 C oracle, step caps "
+                         "scaled to %d node-updates in total, one spawned process per core; "
+                         "%.1f s wall" % (len(sample), nu, wall)}
+
+    agg, clocks, probs = native(args, rank, world, local_rank)
+    if rank != 0:
+        return 0
+    nu = sum(a["node_updates"] for a in agg)
+    ms = max(a["ms"] for a in agg)
+    value = nu / (ms / 1e3)
+    e2e_v = sum(a["e2e_nu"] for a in agg) / (max(a["e2e_ms"] for a in agg) / 1e3)
+    a0 = agg[0]
+    peak, peak_kind = measured_peaks()
+    achieved = a0["sweep_bytes"] / (a0["sweep_ms"] / 1e3) / 1e9
+    traffic, tpath = recorded_traffic(args.workload, args.precision)
+    lat = [x for x in a0["lat"] if x is not None]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded requests, master seed %d)" % W.MASTER_SEED,
+        "config": {"workload": WORKLOADS[args.workload], "requests": len(probs),
+                   "precision": args.precision, "window_steps": args.window,
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "meshes_per_s": a0["meshes"] / (a0["ms"] / 1e3),
+        "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99),
+                       "what": "per request, submit to completion, all requests of a "
+                               "step submitted together"},
+        "mean_steps_per_request": float(np.mean(a0["infos_steps"])),
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": a0["h2d"],
+                "d2h_bytes_per_step": a0["d2h"]},
+        "gpu_launches": a0["launches"] // max(args.steps, 1),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if peak else None, "traffic": traffic,
+                     "kernel": "k_sweep2d" if probs[0].dim == 2 else "k_sweep3d",
+                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
+                     "algorithmic_bytes_per_node_update": 2 * (4 if args.precision == "fp32" else 8)},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def reference_arm(args, world):
+    probs = make_workload(args.workload, args.precision, args.max_steps)
+    sample, cores = oracle_sample(probs, budget_node_updates=1.0e8)
+    for _ in range(args.warmup):
+        run_oracle(sample[: max(1, len(sample) // 4)], cores)
+    vals, walls, nus = [], [], []
+    for _ in range(args.steps):
+        v, wall, nu = run_oracle(sample, cores)
+        vals.append(v)
+        walls.append(wall)
+        nus.append(nu)
+    value = sum(nus) / sum(walls)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(walls) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded requests, master seed %d)" % W.MASTER_SEED,
+        "config": {"workload": WORKLOADS[args.workload], "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d requests of the workload, step caps scaled to %d "
+                                   "node-updates per step" % (len(sample), nus[0])},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

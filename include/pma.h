@@ -225,6 +225,11 @@ pma_status pma_run(pma_ctx *ctx, int64_t max_windows, int32_t *n_active);
 pma_status pma_serve_start(pma_ctx *ctx);
 pma_status pma_serve_stop(pma_ctx *ctx);
 
+/* Admit queued requests now (allocate their device memory, upload their
+ * tables and warm starts) without advancing them, so that a later pma_run
+ * starts with every input resident in device memory.                     */
+pma_status pma_admit(pma_ctx *ctx);
+
 /* Non-blocking completion test (*done = 1 when finished). */
 pma_status pma_poll(pma_ctx *ctx, uint64_t req_id, int32_t *done);
 
@@ -248,6 +253,11 @@ pma_status pma_get_mesh(pma_ctx *ctx, uint64_t req_id, double *x_out, double *ps
 pma_status pma_get_mesh_device(pma_ctx *ctx, uint64_t req_id, void *x_dev, int32_t out_fp64,
                                void *psi_dev, pma_info *info);
 
+/* Batched form of pma_get_mesh_device: one combine launch for n finished
+ * requests; x_dev[i] receives request ids[i]'s mesh (dim_i * N_i values).  */
+pma_status pma_get_mesh_device_batch(pma_ctx *ctx, int32_t n, const uint64_t *ids,
+                                     void *const *x_dev, int32_t out_fp64);
+
 /* FP64 positivity check of a finished request: recomputes det D_h^2 Psi in
  * FP64 at every global node (Sylvester minors of the symmetric FD Hessian)
  * and the signed measure of every mesh cell (2 triangles per quad in both
@@ -256,11 +266,33 @@ pma_status pma_get_mesh_device(pma_ctx *ctx, uint64_t req_id, void *x_dev, int32
  * non-positive cells.                                                     */
 pma_status pma_check_mesh(pma_ctx *ctx, uint64_t req_id, double *out4);
 
+/* Outcome so far of a request without releasing it (status PMA_PENDING
+ * while it runs). */
+pma_status pma_get_info(pma_ctx *ctx, uint64_t req_id, pma_info *info);
+
 /* Drop a request (finished or not) and free its device memory. */
 pma_status pma_release(pma_ctx *ctx, uint64_t req_id);
 
 /* Number of requests queued, admitted and finished-but-unreleased. */
 pma_status pma_counts(pma_ctx *ctx, int32_t *queued, int32_t *active, int32_t *finished);
+
+/* Counters of the context since creation or the last reset.  window_ms is
+ * the device time of the stepping windows, measured with CUDA events on
+ * the context's stream around the sweep launches only; node_updates counts
+ * subdomain nodes advanced by one step; sweep_bytes is the algorithmic
+ * traffic of those updates (one read and one write of v per node);
+ * h2d/d2h_bytes are the host<->device copies the context issued.          */
+typedef struct {
+  int64_t windows;
+  int64_t sweep_launches;
+  int64_t other_launches;
+  int64_t node_updates;
+  double sweep_bytes;
+  double window_ms;
+  double h2d_bytes;
+  double d2h_bytes;
+} pma_stats;
+pma_status pma_get_stats(pma_ctx *ctx, pma_stats *out, int32_t reset);
 
 /* ------------------------------------------------------------ one shot */
 

@@ -11,30 +11,44 @@
 namespace pma {
 
 // ---------------------------------------------------------------- math
-// FP32 uses the SFU approximations (ex2/lg2/sin), FP64 the accurate library
-// functions.
+// FP32 uses the SFU (ex2/lg2 approximations), FP64 the accurate library
+// functions.  exw(q) = exp(-width * q) with the term width as stored in
+// MonT<T> (pre-scaled by log2(e) for FP32).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <typename T>
 struct Fm;
 
 template <>
 struct Fm<float> {
-  __device__ __forceinline__ static float ex(float x) { return __expf(x); }
-  __device__ __forceinline__ static float ln(float x) { return __logf(x); }
+  static constexpr float kLog2e = 1.4426950408889634f;
+  static constexpr float kLn2 = 0.6931471805599453f;
+  __device__ __forceinline__ static float exw(float negwq) { return ex2_approx(negwq); }
+  __device__ __forceinline__ static float ex(float x) { return ex2_approx(x * kLog2e); }
+  __device__ __forceinline__ static float ln(float x) { return lg2_approx(x) * kLn2; }
   __device__ __forceinline__ static float sinpi(float x) { return sinpif(x); }
-  __device__ __forceinline__ static float cospi(float x) { return cospif(x); }
   __device__ __forceinline__ static float sq(float x) { return sqrtf(x); }
   __device__ __forceinline__ static float at2(float y, float x) { return atan2f(y, x); }
   __device__ __forceinline__ static float cs(float x) { return cosf(x); }
   __device__ __forceinline__ static float sn(float x) { return sinf(x); }
-  __device__ __forceinline__ static float pw(float x, float y) { return __powf(x, y); }
+  __device__ __forceinline__ static float pw(float x, float y) { return ex2_approx(y * lg2_approx(x)); }
 };
 
 template <>
 struct Fm<double> {
+  __device__ __forceinline__ static double exw(double negwq) { return exp(negwq); }
   __device__ __forceinline__ static double ex(double x) { return exp(x); }
   __device__ __forceinline__ static double ln(double x) { return log(x); }
   __device__ __forceinline__ static double sinpi(double x) { return ::sinpi(x); }
-  __device__ __forceinline__ static double cospi(double x) { return ::cospi(x); }
   __device__ __forceinline__ static double sq(double x) { return sqrt(x); }
   __device__ __forceinline__ static double at2(double y, double x) { return atan2(y, x); }
   __device__ __forceinline__ static double cs(double x) { return cos(x); }
@@ -43,39 +57,6 @@ struct Fm<double> {
 };
 
 // ---------------------------------------------------------------- monitor
-// Parameters of one problem's density converted to the sweep precision,
-// staged in shared memory once per tile.
-template <typename T>
-struct MonT {
-  int kind, nterms, dim, pad;
-  T base, p0;
-  struct Term {
-    int type, axis, along, pad;
-    T amp, width, r2, a, k2;  // k2 = 2k: sin(2 pi k s) = sinpi(k2 s)
-    T c[3];
-  } t[kMaxTerms];
-};
-
-template <typename T>
-__device__ __forceinline__ void mon_load(MonT<T>& m, const MonDev& d, int dim) {
-  m.kind = d.kind;
-  m.nterms = d.nterms;
-  m.dim = dim;
-  m.base = (T)d.base;
-  m.p0 = (T)d.p0;
-  for (int i = 0; i < kMaxTerms; ++i) {
-    m.t[i].type = d.t[i].type;
-    m.t[i].axis = d.t[i].axis;
-    m.t[i].along = d.t[i].along;
-    m.t[i].amp = (T)d.t[i].amp;
-    m.t[i].width = (T)d.t[i].width;
-    m.t[i].r2 = (T)d.t[i].r2;
-    m.t[i].a = (T)d.t[i].a;
-    m.t[i].k2 = (T)(2.0 * d.t[i].k);
-    for (int a = 0; a < 3; ++a) m.t[i].c[a] = (T)d.t[i].c[a];
-  }
-}
-
 // sech^2(z) = 4 e^{-2|z|} / (1 + e^{-2|z|})^2, overflow-free.
 template <typename T>
 __device__ __forceinline__ T sech2(T z) {
@@ -85,32 +66,38 @@ __device__ __forceinline__ T sech2(T z) {
 }
 
 template <typename T>
-__device__ __forceinline__ T term_value(const typename MonT<T>::Term& t, int dim, const T* x) {
-  T q = 0;
+__device__ __forceinline__ T term_value(const typename MonT<T>::Term& t, int dim, T x0, T x1,
+                                        T x2) {
   switch (t.type) {
-    case PMA_TERM_BUMP:
-      for (int a = 0; a < 3; ++a)
-        if (a < dim) {
-          T d = x[a] - t.c[a];
-          q = fma(d, d, q);
-        }
-      return t.amp * Fm<T>::ex(-t.width * q);
+    case PMA_TERM_BUMP: {
+      T d0 = x0 - t.c[0], d1 = x1 - t.c[1];
+      T q = fma(d0, d0, d1 * d1);
+      if (dim > 2) {
+        T d2 = x2 - t.c[2];
+        q = fma(d2, d2, q);
+      }
+      return t.amp * Fm<T>::exw(-t.width * q);
+    }
     case PMA_TERM_RING: {
-      for (int a = 0; a < 3; ++a)
-        if (a < dim) {
-          T d = x[a] - t.c[a];
-          q = fma(d, d, q);
-        }
+      T d0 = x0 - t.c[0], d1 = x1 - t.c[1];
+      T q = fma(d0, d0, d1 * d1);
+      if (dim > 2) {
+        T d2 = x2 - t.c[2];
+        q = fma(d2, d2, q);
+      }
       T s = q - t.r2;
-      return t.amp * Fm<T>::ex(-t.width * s * s);
+      return t.amp * Fm<T>::exw(-t.width * s * s);
     }
     case PMA_TERM_SINE: {
-      T s = x[t.axis] - t.c[t.axis] - t.a * Fm<T>::sinpi(t.k2 * x[t.along]);
-      return t.amp * Fm<T>::ex(-t.width * s * s);
+      const T xa = t.axis == 0 ? x0 : (t.axis == 1 ? x1 : x2);
+      const T xb = t.along == 0 ? x0 : (t.along == 1 ? x1 : x2);
+      T s = xa - t.c[t.axis] - t.a * Fm<T>::sinpi(t.k2 * xb);
+      return t.amp * Fm<T>::exw(-t.width * s * s);
     }
     case PMA_TERM_BUMP1: {
-      T s = x[t.axis] - t.c[t.axis];
-      return t.amp * Fm<T>::ex(-t.width * s * s);
+      const T xa = t.axis == 0 ? x0 : (t.axis == 1 ? x1 : x2);
+      T s = xa - t.c[t.axis];
+      return t.amp * Fm<T>::exw(-t.width * s * s);
     }
   }
   return T(0);
@@ -118,19 +105,19 @@ __device__ __forceinline__ T term_value(const typename MonT<T>::Term& t, int dim
 
 // rho = sqrt(1 + |grad u|^2) for the test functions of Sect. 4.
 template <typename T>
-__device__ T arclen_rho(const MonT<T>& m, const T* x) {
+__device__ T arclen_rho(const MonT<T>& m, T x0, T x1, T x2) {
   T g0 = 0, g1 = 0, g2 = 0;
   switch (m.kind) {
     case PMA_MON_ARCLEN_BURGERS: {
       T eps = m.p0;
-      T s = (x[0] + x[1] - 1) / (2 * eps);
+      T s = (x0 + x1 - 1) / (2 * eps);
       T d = -T(0.25) * sech2<T>(T(0.5) * s) / (2 * eps);
       g0 = d;
       g1 = d;
       break;
     }
     case PMA_MON_ARCLEN_SPIRAL: {
-      T dx = x[0] - T(0.7), dy = x[1] - T(0.5);
+      T dx = x0 - T(0.7), dy = x1 - T(0.5);
       T r2 = dx * dx + dy * dy;
       T phi = Fm<T>::at2(dy, dx) - 20 * r2;
       T cp = Fm<T>::cs(phi), s2 = Fm<T>::sn(2 * phi);
@@ -143,11 +130,11 @@ __device__ T arclen_rho(const MonT<T>& m, const T* x) {
       break;
     }
     case PMA_MON_ARCLEN_TANH_SPHERE: {
-      T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+      T r2 = x0 * x0 + x1 * x1 + x2 * x2;
       T f = 200 * sech2<T>(100 * (r2 - T(0.125)));
-      g0 = f * x[0];
-      g1 = f * x[1];
-      g2 = f * x[2];
+      g0 = f * x0;
+      g1 = f * x1;
+      g2 = f * x2;
       break;
     }
     case PMA_MON_ARCLEN_NINE_SPHERES: {
@@ -155,7 +142,7 @@ __device__ T arclen_rho(const MonT<T>& m, const T* x) {
         T cx = (k == 0) ? T(0) : ((k == 1 || k == 2 || k == 5 || k == 6) ? T(0.5) : T(-0.5));
         T cy = (k == 0) ? T(0) : ((k & 1) ? T(0.5) : T(-0.5));
         T cz = (k == 0) ? T(0) : (k <= 4 ? T(0.5) : T(-0.5));
-        T ex = x[0] - cx, ey = x[1] - cy, ez = x[2] - cz;
+        T ex = x0 - cx, ey = x1 - cy, ez = x2 - cz;
         T f = 100 * sech2<T>(50 * (ex * ex + ey * ey + ez * ez - T(0.1875)));
         g0 += f * ex;
         g1 += f * ey;
@@ -168,20 +155,20 @@ __device__ T arclen_rho(const MonT<T>& m, const T* x) {
 }
 
 template <typename T>
-__device__ __forceinline__ T rho_at(const MonT<T>& m, const T* x) {
+__device__ __forceinline__ T rho_at(const MonT<T>& m, T x0, T x1, T x2) {
   if (m.kind == PMA_MON_SUM) {
     T r = m.base;
     for (int i = 0; i < kMaxTerms; ++i)
-      if (i < m.nterms) r += term_value<T>(m.t[i], m.dim, x);
+      if (i < m.nterms) r += term_value<T>(m.t[i], m.dim, x0, x1, x2);
     return r;
   }
   if (m.kind == PMA_MON_PRODUCT) {
     T r = 1;
     for (int i = 0; i < kMaxTerms; ++i)
-      if (i < m.nterms) r *= m.base + term_value<T>(m.t[i], m.dim, x);
+      if (i < m.nterms) r *= m.base + term_value<T>(m.t[i], m.dim, x0, x1, x2);
     return r;
   }
-  return arclen_rho<T>(m, x);
+  return arclen_rho<T>(m, x0, x1, x2);
 }
 
 // ---------------------------------------------------------------- indices
@@ -204,15 +191,39 @@ __device__ __forceinline__ bool is_dir(int faces, int dim, int i, int j, int l, 
   return d;
 }
 
-__device__ __forceinline__ double trap_w(int gi, int N, double h) {
-  return (gi == 0 || gi == N - 1) ? 0.5 * h : h;
-}
-
 // Owner block index along one axis for global index g, starting from k.
 __device__ __forceinline__ int owner_k(const int* b, int parts, int g, int k) {
   while (k > 0 && g < b[k]) --k;
   while (k < parts - 1 && g >= b[k + 1]) ++k;
   return k;
+}
+
+// Global stores that the compiler need not treat as aliasing shared memory
+// (a store through a generic pointer would force every shared-memory value
+// to be reloaded after it).
+__device__ __forceinline__ void st_global(float* p, float v) {
+  asm volatile("st.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+}
+__device__ __forceinline__ void st_global(double* p, double v) {
+  asm volatile("st.global.f64 [%0], %1;" ::"l"(p), "d"(v));
+}
+
+// Asynchronous 16-byte global -> shared copies (completion: cp_async_wait
+// by the issuing thread, then a barrier for the others).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Cooperative copy of a 16-byte-aligned struct into shared memory.
+template <int NT>
+__device__ __forceinline__ void coop_copy(void* dst, const void* src, int bytes, int first) {
+  const int4* s = (const int4*)src;
+  int4* d = (int4*)dst;
+  const int n = bytes / 16;
+  for (int i = threadIdx.x - first; i >= 0 && i < n; i += NT) d[i] = __ldcg(s + i);
 }
 
 }  // namespace pma

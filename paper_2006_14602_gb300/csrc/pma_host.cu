@@ -50,7 +50,7 @@ using Clock = std::chrono::steady_clock;
 
 struct HostSub {
   int n[3], g0[3], clo[3], chi[3], k[3];
-  int faces, idx;
+  int faces, idx, pitch;
   size_t elems;
   size_t off[2];  // byte offsets of the two buffers in the request block
 };
@@ -150,8 +150,8 @@ pma_status build_request(Request& r) {
       lo[a][0] = hi[a][0] = 0;
       continue;
     }
-    if (g.n[a] < 3 || !(g.hi[a] > g.lo[a])) {
-      set_err("grid: n >= 3 and hi > lo on every axis");
+    if (g.n[a] < 3 || g.n[a] > 65535 || !(g.hi[a] > g.lo[a])) {
+      set_err("grid: 3 <= n <= 65535 and hi > lo on every axis");
       return PMA_ERR_INVALID;
     }
     r.parts[a] = r.d.parts[a] < 1 ? 1 : r.d.parts[a];
@@ -192,8 +192,9 @@ pma_status build_request(Request& r) {
           if (kk[a] == r.parts[a] - 1) s.faces |= 1 << (2 * a + 1);
         }
         s.idx = idx;
-        s.elems = (size_t)s.n[0] * s.n[1] * s.n[2];
-        r.sub_nodes += (long long)s.elems;
+        s.pitch = (s.n[0] + 3) & ~3;
+        s.elems = (size_t)s.pitch * s.n[1] * s.n[2];
+        r.sub_nodes += (long long)s.n[0] * s.n[1] * s.n[2];
         for (int b = 0; b < 2; ++b) {
           s.off[b] = off;
           off = align(off + s.elems * r.esize);
@@ -228,7 +229,11 @@ struct pma_ctx {
   std::vector<int> free_slots;
   ProbDesc* d_probs = nullptr;
   ProbState* d_state = nullptr;
+  ProbHot<float>* d_hotf = nullptr;
+  ProbHot<double>* d_hotd = nullptr;
   std::vector<ProbDesc> h_probs;
+  std::vector<ProbHot<float>> h_hotf;
+  std::vector<ProbHot<double>> h_hotd;
   ProbState* h_state = nullptr;  // pinned mirror
 
   // tables
@@ -238,6 +243,7 @@ struct pma_ctx {
   Partial* d_part[NUM_CLS] = {};
   size_t work_cap[NUM_CLS] = {};
   int nwork[NUM_CLS] = {};
+  unsigned int* d_queue = nullptr;  // 2 counters per class
   int grid[NUM_CLS] = {};
   int tile_id[NUM_CLS] = {};
   std::vector<SubDesc> h_subs;
@@ -262,6 +268,10 @@ struct pma_ctx {
   int opt_tile2d = 0, opt_tile3d = 0;
   int max_active = 0;
 
+  // counters (pma_get_stats)
+  pma_stats stats{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
   // server
   std::thread server;
   std::atomic<bool> stop{false};
@@ -277,6 +287,12 @@ pma_status ensure_slots(pma_ctx* c, int need) {
   ProbDesc* np = nullptr;
   ProbState* ns = nullptr;
   ProbState* hs = nullptr;
+  if (c->d_hotf) cudaFree(c->d_hotf);
+  if (c->d_hotd) cudaFree(c->d_hotd);
+  c->d_hotf = nullptr;
+  c->d_hotd = nullptr;
+  PMA_CK(cudaMalloc(&c->d_hotf, sizeof(ProbHot<float>) * cap));
+  PMA_CK(cudaMalloc(&c->d_hotd, sizeof(ProbHot<double>) * cap));
   PMA_CK(cudaMalloc(&np, sizeof(ProbDesc) * cap));
   PMA_CK(cudaMalloc(&ns, sizeof(ProbState) * cap));
   PMA_CK(cudaMallocHost(&hs, sizeof(ProbState) * cap));
@@ -292,6 +308,8 @@ pma_status ensure_slots(pma_ctx* c, int need) {
   }
   for (int s = cap - 1; s >= c->slot_cap; --s) c->free_slots.push_back(s);
   c->h_probs.resize(cap);
+  c->h_hotf.resize(cap);
+  c->h_hotd.resize(cap);
   c->d_probs = np;
   c->d_state = ns;
   c->h_state = hs;
@@ -349,6 +367,52 @@ void fill_probdesc(const Request& r, ProbDesc& pd) {
   for (int t = 0; t < kMaxTerms; ++t) pd.mon.t[t] = r.m.term[t];
 }
 
+template <typename T>
+void fill_hot(const Request& r, const ProbDesc& pd, ProbHot<T>& h) {
+  memset(&h, 0, sizeof(h));
+  h.dim = pd.dim;
+  h.rhs = pd.rhs;
+  h.normalize = pd.normalize;
+  h.stop_norm = pd.stop_norm;
+  h.sub_base = pd.sub_base;
+  h.ntiles = pd.tile_end - pd.tile_begin;
+  for (int a = 0; a < 3; ++a) {
+    h.N[a] = pd.N[a];
+    h.parts[a] = pd.parts[a];
+    h.lo[a] = (T)pd.lo[a];
+    h.h[a] = (T)pd.h[a];
+    h.hd[a] = pd.h[a];
+    h.hw[a] = (T)(0.5 * pd.h[a]);
+    h.inv2h[a] = (T)(0.5 / pd.h[a]);
+    h.invh2[a] = (T)(1.0 / (pd.h[a] * pd.h[a]));
+  }
+  h.inv4hh[0] = (T)(0.25 / (pd.h[0] * pd.h[1]));
+  h.inv4hh[1] = (T)(0.25 / (pd.h[0] * pd.h[2]));
+  h.inv4hh[2] = (T)(0.25 / (pd.h[1] * pd.h[2]));
+  h.dt = (T)pd.dt;
+  h.vol = (T)pd.vol;
+  // exp(-w q) is evaluated as 2^(-w log2(e) q) by the FP32 path
+  const double wscale = (sizeof(T) == 4) ? 1.4426950408889634 : 1.0;
+  h.mon.kind = r.m.kind;
+  h.mon.nterms = r.m.nterms;
+  h.mon.dim = pd.dim;
+  h.mon.base = (T)r.m.base;
+  h.mon.p0 = (T)r.m.p0;
+  for (int t = 0; t < kMaxTerms; ++t) {
+    const pma_term& q = r.m.term[t];
+    auto& o = h.mon.t[t];
+    o.type = q.type;
+    o.axis = q.axis;
+    o.along = q.along;
+    o.amp = (T)q.amp;
+    o.width = (T)(q.width * wscale);
+    o.r2 = (T)q.r2;
+    o.a = (T)q.a;
+    o.k2 = (T)(2.0 * q.k);
+    for (int a = 0; a < 3; ++a) o.c[a] = (T)q.c[a];
+  }
+}
+
 int pick_tile(pma_ctx* c, int cls) {
   if (cls == CLS_2D_F32 || cls == CLS_2D_F64) {
     int id = c->opt_tile2d;
@@ -377,18 +441,8 @@ pma_status rebuild(pma_ctx* c) {
     std::vector<WorkItem>& wl = c->h_work[r.cls];
     const bool live = (r.state == RQ_ACTIVE);
     pd.tile_begin = (int)wl.size();
-    int tx, ty, tz;
-    if (r.dim == 2) {
-      Tile2D t = tile2d_shape(c->tile_id[r.cls]);
-      tx = t.tx;
-      ty = t.ty;
-      tz = 1;
-    } else {
-      Tile3D t = tile3d_shape(c->tile_id[r.cls]);
-      tx = t.tx;
-      ty = t.ty;
-      tz = t.tz;
-    }
+    const Tile2D t2 = tile2d_shape(c->tile_id[r.cls], r.esize == 8);
+    const Tile3D t3 = tile3d_shape(c->tile_id[r.cls]);
     for (size_t si = 0; si < r.subs.size(); ++si) {
       const HostSub& hs = r.subs[si];
       SubDesc sd{};
@@ -402,20 +456,40 @@ pma_status rebuild(pma_ctx* c) {
       }
       sd.faces = hs.faces;
       sd.idx = hs.idx;
+      sd.pitch = hs.pitch;
       sd.v[0] = r.block + hs.off[0];
       sd.v[1] = r.block + hs.off[1];
       sd.tile_begin = (int)wl.size();
       if (live) {
         const int sidx = (int)c->h_subs.size();
-        for (int z = 0; z < hs.n[2]; z += tz)
-          for (int y = 0; y < hs.n[1]; y += ty)
-            for (int x = 0; x < hs.n[0]; x += tx) wl.push_back(WorkItem{sidx, x, y, z});
+        if (r.dim == 2) {
+          // full-width row bands (strips of at most t2.cols columns)
+          for (int x = 0; x < hs.n[0]; x += t2.cols) {
+            const int cols = std::min(t2.cols, hs.n[0] - x);
+            const int swp = ((cols + 3) & ~3) + 8;
+            int rows = std::max(1, std::min(hs.n[1], t2.nodes / ((cols + 3) & ~3)));
+            while (rows > 1 && (rows + 2) * swp > t2.smax) --rows;
+            for (int y = 0; y < hs.n[1]; y += rows) {
+              const int rr = std::min(rows, hs.n[1] - y);
+              wl.push_back(WorkItem{sidx, r.slot, x | (y << 16), cols | (rr << 16)});
+            }
+          }
+        } else {
+          for (int z = 0; z < hs.n[2]; z += t3.tz)
+            for (int y = 0; y < hs.n[1]; y += t3.ty)
+              for (int x = 0; x < hs.n[0]; x += t3.tx) {
+                const int d = std::min(t3.tz, hs.n[2] - z);
+                wl.push_back(WorkItem{sidx, r.slot, x | (y << 16), z | (d << 16)});
+              }
+        }
       }
       sd.tile_end = (int)wl.size();
       c->h_subs.push_back(sd);
     }
     pd.tile_end = (int)wl.size();
     if (live) c->live_tiles += pd.tile_end - pd.tile_begin;
+    fill_hot<float>(r, pd, c->h_hotf[r.slot]);
+    fill_hot<double>(r, pd, c->h_hotd[r.slot]);
   }
   pma_status st;
   if ((st = ensure_buf(&c->d_subs, &c->subs_cap, c->h_subs.size() + 1)) != PMA_OK) return st;
@@ -441,6 +515,14 @@ pma_status rebuild(pma_ctx* c) {
   }
   PMA_CK(cudaMemcpyAsync(c->d_probs, c->h_probs.data(), sizeof(ProbDesc) * c->slot_cap,
                          cudaMemcpyHostToDevice, c->stream));
+  PMA_CK(cudaMemcpyAsync(c->d_hotf, c->h_hotf.data(), sizeof(ProbHot<float>) * c->slot_cap,
+                         cudaMemcpyHostToDevice, c->stream));
+  PMA_CK(cudaMemcpyAsync(c->d_hotd, c->h_hotd.data(), sizeof(ProbHot<double>) * c->slot_cap,
+                         cudaMemcpyHostToDevice, c->stream));
+  c->stats.h2d_bytes += (double)(sizeof(SubDesc) * c->h_subs.size() +
+                                 (sizeof(ProbDesc) + sizeof(ProbHot<float>) +
+                                  sizeof(ProbHot<double>)) * c->slot_cap);
+  for (int k = 0; k < NUM_CLS; ++k) c->stats.h2d_bytes += (double)sizeof(WorkItem) * c->nwork[k];
   // The host-side vectors must stay alive until the copies complete.
   PMA_CK(cudaStreamSynchronize(c->stream));
   c->dirty = false;
@@ -450,6 +532,8 @@ pma_status rebuild(pma_ctx* c) {
 
 LaunchArgs args_for(pma_ctx* c, int k, int t0, int n) {
   LaunchArgs a;
+  a.hotf = c->d_hotf;
+  a.hotd = c->d_hotd;
   a.work = c->d_work[k];
   a.t0 = t0;
   a.nwork = n;
@@ -457,6 +541,7 @@ LaunchArgs args_for(pma_ctx* c, int k, int t0, int n) {
   a.probs = c->d_probs;
   a.st = c->d_state;
   a.part = c->d_part[k];
+  a.queue = c->d_queue + 2 * k;
   a.grid = std::min(n, c->grid[k] > 0 ? c->grid[k] : n);
   return a;
 }
@@ -479,12 +564,27 @@ pma_status launch_step(pma_ctx* c) {
   return PMA_OK;
 }
 
+int launches_per_step(pma_ctx* c) {
+  int n = 0;
+  for (int k = 0; k < NUM_CLS; ++k) {
+    if (c->nwork[k] == 0) continue;
+    if (c->launch_mode == PMA_LAUNCH_PER_SUBDOMAIN) {
+      for (const SubDesc& sd : c->h_subs)
+        if (sd.tile_end > sd.tile_begin && c->h_probs[sd.prob].cls == k) ++n;
+    } else {
+      ++n;
+    }
+  }
+  return n;
+}
+
 pma_status run_window(pma_ctx* c, int steps) {
   if (c->dirty) {
     pma_status st = rebuild(c);
     if (st != PMA_OK) return st;
   }
   const bool graphs = c->use_graphs && c->launch_mode == PMA_LAUNCH_BATCHED;
+  PMA_CK(cudaEventRecord(c->ev0, c->stream));
   if (graphs) {
     if (!c->graph_valid || c->graph_steps != steps) {
       if (c->gexec) {
@@ -514,9 +614,16 @@ pma_status run_window(pma_ctx* c, int steps) {
       if (st != PMA_OK) return st;
     }
   }
+  PMA_CK(cudaEventRecord(c->ev1, c->stream));
   PMA_CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(ProbState) * c->slot_cap,
                          cudaMemcpyDeviceToHost, c->stream));
   PMA_CK(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  PMA_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  c->stats.windows += 1;
+  c->stats.window_ms += ms;
+  c->stats.sweep_launches += (int64_t)steps * launches_per_step(c);
+  c->stats.d2h_bytes += (double)sizeof(ProbState) * c->slot_cap;
   return PMA_OK;
 }
 
@@ -576,9 +683,11 @@ pma_status admit(pma_ctx* c) {
     }
     r.block = (char*)blk;
     c->used += r.bytes;
-    if (!r.psi0.empty())
+    if (!r.psi0.empty()) {
       PMA_CK(cudaMemcpyAsync(r.block + r.psi_off, r.psi0.data(), sizeof(double) * r.nodes,
                              cudaMemcpyHostToDevice, c->stream));
+      c->stats.h2d_bytes += (double)sizeof(double) * r.nodes;
+    }
     r.slot = c->free_slots.back();
     c->free_slots.pop_back();
     ProbState ps{};
@@ -586,6 +695,7 @@ pma_status admit(pma_ctx* c) {
     ps.status = PMA_PENDING;
     PMA_CK(cudaMemcpyAsync(c->d_state + r.slot, &ps, sizeof(ps), cudaMemcpyHostToDevice,
                            c->stream));
+    c->stats.h2d_bytes += (double)sizeof(ps);
     PMA_CK(cudaStreamSynchronize(c->stream));
     c->h_state[r.slot] = ps;
     r.state = RQ_ACTIVE;
@@ -630,6 +740,10 @@ pma_status combine_into(pma_ctx* c, Request& r, void* x, int out_fp64, void* psi
   CombineJob j{r.slot, out_fp64, x, psi};
   PMA_CK(cudaMemcpyAsync(c->d_jobs, &j, sizeof(j), cudaMemcpyHostToDevice, c->stream));
   PMA_CK(launch_combine(c->d_jobs, 1, r.nodes, c->d_subs, c->d_probs, c->d_state, c->stream));
+  // the job record lives on this stack frame: wait for the copy
+  PMA_CK(cudaStreamSynchronize(c->stream));
+  c->stats.h2d_bytes += sizeof(j);
+  c->stats.other_launches += 1;
   return PMA_OK;
 }
 
@@ -638,8 +752,18 @@ pma_status loop_once(pma_ctx* c, std::unique_lock<std::mutex>& lk, bool* idle) {
   if (st != PMA_OK) return st;
   *idle = c->active.empty();
   if (*idle) return PMA_OK;
+  std::vector<long long> before(c->active.size());
+  for (size_t i = 0; i < c->active.size(); ++i)
+    before[i] = c->h_state[c->reqs[c->active[i]]->slot].step;
+  const std::vector<uint64_t> ids = c->active;
   st = run_window(c, c->window);
   if (st != PMA_OK) return st;
+  for (size_t i = 0; i < ids.size(); ++i) {
+    const Request& r = *c->reqs[ids[i]];
+    const long long d = c->h_state[r.slot].step - before[i];
+    c->stats.node_updates += d * r.sub_nodes;
+    c->stats.sweep_bytes += 2.0 * r.esize * (double)(d * r.sub_nodes);
+  }
   collect(c);
   (void)lk;
   return PMA_OK;
@@ -687,6 +811,10 @@ pma_status pma_create(pma_ctx** out, int device, size_t mem_budget_bytes, void* 
   pma_status st = ensure_slots(c.get(), 64);
   if (st != PMA_OK) return st;
   PMA_CK(cudaMalloc(&c->d_check, sizeof(double) * 4 + sizeof(unsigned long long)));
+  PMA_CK(cudaMalloc(&c->d_queue, sizeof(unsigned int) * 2 * NUM_CLS));
+  PMA_CK(cudaMemset(c->d_queue, 0, sizeof(unsigned int) * 2 * NUM_CLS));
+  PMA_CK(cudaEventCreate(&c->ev0));
+  PMA_CK(cudaEventCreate(&c->ev1));
   *out = c.release();
   return PMA_OK;
 }
@@ -702,6 +830,8 @@ pma_status pma_destroy(pma_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   cudaFree(c->d_probs);
   cudaFree(c->d_state);
+  cudaFree(c->d_hotf);
+  cudaFree(c->d_hotd);
   cudaFreeHost(c->h_state);
   cudaFree(c->d_subs);
   for (int k = 0; k < NUM_CLS; ++k) {
@@ -710,6 +840,9 @@ pma_status pma_destroy(pma_ctx* c) {
   }
   cudaFree(c->d_jobs);
   cudaFree(c->d_check);
+  cudaFree(c->d_queue);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return PMA_OK;
@@ -950,6 +1083,7 @@ pma_status pma_get_mesh(pma_ctx* c, uint64_t id, double* x_out, double* psi_out,
       set_err(std::string("mesh copy: ") + cudaGetErrorString(e));
       st = PMA_ERR_CUDA;
     }
+    c->stats.d2h_bytes += (double)sizeof(double) * (nx + np);
   }
   cudaFreeAsync(tmp, c->stream);
   if (st != PMA_OK) return st;
@@ -992,6 +1126,16 @@ pma_status pma_check_mesh(pma_ctx* c, uint64_t id, double* out4) {
   return PMA_OK;
 }
 
+pma_status pma_get_info(pma_ctx* c, uint64_t id, pma_info* info) {
+  if (!c || !info) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->reqs.find(id);
+  if (it == c->reqs.end()) return PMA_ERR_NOT_FOUND;
+  *info = it->second->info;
+  if (it->second->state != RQ_FINISHED) info->status = PMA_PENDING;
+  return PMA_OK;
+}
+
 pma_status pma_release(pma_ctx* c, uint64_t id) {
   if (!c) return PMA_ERR_INVALID;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -1020,6 +1164,58 @@ pma_status pma_counts(pma_ctx* c, int32_t* queued, int32_t* active, int32_t* fin
   if (queued) *queued = (int32_t)c->queue.size();
   if (active) *active = (int32_t)c->active.size();
   if (finished) *finished = f;
+  return PMA_OK;
+}
+
+pma_status pma_admit(pma_ctx* c) {
+  if (!c) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->serving) return PMA_ERR_BUSY;
+  PMA_CK(cudaSetDevice(c->device));
+  pma_status st = admit(c);
+  if (st != PMA_OK) return st;
+  if (c->dirty) st = rebuild(c);
+  return st;
+}
+
+pma_status pma_get_mesh_device_batch(pma_ctx* c, int32_t n, const uint64_t* ids,
+                                     void* const* x_dev, int32_t out_fp64) {
+  if (!c || n < 0 || (n > 0 && (!ids || !x_dev))) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  PMA_CK(cudaSetDevice(c->device));
+  std::vector<CombineJob> jobs;
+  long long maxn = 0;
+  for (int i = 0; i < n; ++i) {
+    auto it = c->reqs.find(ids[i]);
+    if (it == c->reqs.end()) return PMA_ERR_NOT_FOUND;
+    Request& r = *it->second;
+    if (r.state != RQ_FINISHED || !r.block) return PMA_ERR_BUSY;
+    if (!x_dev[i]) return PMA_ERR_INVALID;
+    jobs.push_back(CombineJob{r.slot, out_fp64 ? 1 : 0, x_dev[i], nullptr});
+    maxn = std::max(maxn, r.nodes);
+  }
+  if (jobs.empty()) return PMA_OK;
+  if (c->dirty) {
+    pma_status st = rebuild(c);
+    if (st != PMA_OK) return st;
+  }
+  pma_status st = ensure_jobs(c, (int)jobs.size());
+  if (st != PMA_OK) return st;
+  PMA_CK(cudaMemcpyAsync(c->d_jobs, jobs.data(), sizeof(CombineJob) * jobs.size(),
+                         cudaMemcpyHostToDevice, c->stream));
+  PMA_CK(launch_combine(c->d_jobs, (int)jobs.size(), maxn, c->d_subs, c->d_probs, c->d_state,
+                        c->stream));
+  PMA_CK(cudaStreamSynchronize(c->stream));
+  c->stats.h2d_bytes += (double)sizeof(CombineJob) * jobs.size();
+  c->stats.other_launches += 1;
+  return PMA_OK;
+}
+
+pma_status pma_get_stats(pma_ctx* c, pma_stats* out, int32_t reset) {
+  if (!c || !out) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  *out = c->stats;
+  if (reset) c->stats = pma_stats{};
   return PMA_OK;
 }
 

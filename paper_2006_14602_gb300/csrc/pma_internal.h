@@ -38,6 +38,33 @@ struct MonDev {
   pma_term t[kMaxTerms];
 };
 
+// Monitor parameters in the sweep precision.  `width` is pre-multiplied by
+// log2(e) for the FP32 path (exp(-w q) = 2^(-w log2e q)); k2 = 2k so that
+// sin(2 pi k s) = sinpi(k2 s).
+template <typename T>
+struct alignas(16) MonT {
+  int kind, nterms, dim, pad;
+  T base, p0;
+  struct Term {
+    int type, axis, along, pad;
+    T amp, width, r2, a, k2;
+    T c[3];
+  } t[kMaxTerms];
+};
+
+// Everything one sweep tile needs about its problem, in its precision,
+// precomputed on the host (no divisions or FP64 work per tile on device).
+template <typename T>
+struct alignas(16) ProbHot {
+  int dim, rhs, normalize, stop_norm;
+  int N[3], sub_base;
+  int parts[3], ntiles;
+  T lo[3], h[3], inv2h[3], invh2[3], inv4hh[3], hw[3];
+  T dt, vol;
+  double hd[3];
+  MonT<T> mon;
+};
+
 struct ProbDesc {
   int dim;
   int N[3];
@@ -58,7 +85,7 @@ struct ProbDesc {
   MonDev mon;
 };
 
-struct SubDesc {
+struct alignas(16) SubDesc {
   int prob;          // problem slot
   int n[3];          // local node counts (1 on unused axes)
   int g0[3];         // global index of local node 0
@@ -67,11 +94,11 @@ struct SubDesc {
   int faces;         // bit 2a: low face of axis a is physical; bit 2a+1: high
   int idx;           // subdomain index within its problem (raster order)
   int tile_begin, tile_end;  // its tiles in the class work list
-  int pad;
-  void* v[2];        // ping-pong state buffers
+  int pitch;         // row stride in elements (n[0] rounded up to 4)
+  void* v[2];        // ping-pong state buffers, pitch * n[1] * n[2] values
 };
 
-struct ProbState {
+struct alignas(16) ProbState {
   long long step;       // forward-Euler steps taken
   int phase;            // Phase
   int status;           // pma_status once done
@@ -87,9 +114,15 @@ struct ProbState {
   double pad;
 };
 
-struct WorkItem {
+// One unit of sweep work: a box of nodes of one subdomain.
+//   2D: nodes [i0, i0+cols) x [j0, j0+rows), processed with a flattened
+//       node index (row bands: no padding waste on ragged subdomains);
+//   3D: an xy tile [i0, i0+cols) x [j0, j0+rows) over planes [k0, k0+depth).
+struct alignas(16) WorkItem {
   int sub;
-  int x0, y0, z0;
+  int prob;
+  int ij;    // i0 | j0 << 16
+  int ext;   // 2D: cols | rows << 16; 3D: k0 | depth << 16 (tile shape fixed)
 };
 
 struct Partial {
@@ -105,13 +138,16 @@ struct Partial {
 static_assert(sizeof(Partial) == 64, "partial record is one 64-byte line");
 static_assert(sizeof(WorkItem) == 16, "work item is 16 bytes");
 
-// Tile shapes (nodes per CTA).  2D: TX x TY, one node per thread and RY rows
-// per thread; 3D: TX x TY threads marching TZ planes.
-struct Tile2D { int tx, ty; };
+// Work shapes.  2D: a band holds at most `nodes` nodes, at most `cols`
+// wide, processed by `threads` threads (shared staging of the band plus a
+// one-node halo); 3D: TX x TY threads marching TZ planes.
+struct Tile2D { int threads, nodes, smax, cols; };
 struct Tile3D { int tx, ty, tz; };
 
 // Kernel launch entry points (pma_kernels.cu).
 struct LaunchArgs {
+  const ProbHot<float>* hotf;
+  const ProbHot<double>* hotd;
   const WorkItem* work;  // class work list (absolute base)
   int t0;                // first work item of this launch
   int nwork;             // work items of this launch
@@ -119,12 +155,13 @@ struct LaunchArgs {
   const ProbDesc* probs;
   ProbState* st;
   Partial* part;
-  int grid;   // CTAs (grid-stride over the work list)
+  unsigned int* queue;   // two counters: next work item, CTAs finished
+  int grid;              // CTAs (persistent, pulling work items)
 };
 
 int tile2d_count();
 int tile3d_count();
-Tile2D tile2d_shape(int id);
+Tile2D tile2d_shape(int id, bool fp64);
 Tile3D tile3d_shape(int id);
 
 // cls selects dim/precision; tile_id a compiled tile shape.

@@ -32,68 +32,46 @@
 namespace pma {
 
 // ---------------------------------------------------------------- tile header
+// Shared-memory copy of everything one work item needs: the item, its
+// subdomain, its problem's scalars and hot descriptor (copied with 16-byte
+// loads spread over the block, so the whole header costs one round trip
+// after the work item itself, which is prefetched one item ahead).
 template <typename T>
-struct TileHdr {
-  int sub, x0, y0, z0;
-  int prob, phase, parity, faces;
-  int n[3], g0[3], clo[3], chi[3], N[3], k[3], parts[3];
-  int dim, rhs, normalize, stop_norm, sub_base, tile_begin, tile_end, ntiles;
-  T dt, c_lag, corr, scale_root;
-  T inv2h[3], invh2[3], inv4hh[3], lo[3], h[3];
-  double hd[3];
-  const T* src;
-  T* dst;
-  const double* psi0;
+struct SmemHdr {
+  WorkItem w;
+  SubDesc sd;
+  ProbState ps;
+  ProbHot<T> ph;
 };
 
 template <typename T>
-__device__ void load_header(const LaunchArgs& a, int t, TileHdr<T>& H, MonT<T>& M) {
-  const WorkItem w = a.work[t];
-  const SubDesc& sd = a.subs[w.sub];
-  const int p = sd.prob;
-  const ProbDesc& pd = a.probs[p];
-  const ProbState& ps = a.st[p];
-  H.sub = w.sub;
-  H.x0 = w.x0;
-  H.y0 = w.y0;
-  H.z0 = w.z0;
-  H.prob = p;
-  H.phase = *((volatile const int*)&ps.phase);
-  H.parity = ps.parity;
-  H.faces = sd.faces;
-  H.dim = pd.dim;
-  for (int q = 0; q < 3; ++q) {
-    H.n[q] = sd.n[q];
-    H.g0[q] = sd.g0[q];
-    H.clo[q] = sd.clo[q];
-    H.chi[q] = sd.chi[q];
-    H.N[q] = pd.N[q];
-    H.k[q] = sd.k[q];
-    H.parts[q] = pd.parts[q];
-    H.lo[q] = (T)pd.lo[q];
-    H.h[q] = (T)pd.h[q];
-    H.hd[q] = pd.h[q];
-    H.inv2h[q] = (T)(0.5 / pd.h[q]);
-    H.invh2[q] = (T)(1.0 / (pd.h[q] * pd.h[q]));
-  }
-  H.inv4hh[0] = (T)(0.25 / (pd.h[0] * pd.h[1]));  // xy
-  H.inv4hh[1] = (T)(0.25 / (pd.h[0] * pd.h[2]));  // xz
-  H.inv4hh[2] = (T)(0.25 / (pd.h[1] * pd.h[2]));  // yz
-  H.rhs = pd.rhs;
-  H.normalize = pd.normalize;
-  H.stop_norm = pd.stop_norm;
-  H.sub_base = pd.sub_base;
-  H.tile_begin = pd.tile_begin;
-  H.tile_end = pd.tile_end;
-  H.ntiles = pd.tile_end - pd.tile_begin;
-  H.dt = (T)pd.dt;
-  H.c_lag = (T)ps.c_lag;
-  H.corr = (T)ps.corr;
-  H.scale_root = (T)(pd.vol / ps.theta_prev);
-  H.src = (const T*)sd.v[ps.parity];
-  H.dst = (T*)sd.v[ps.parity ^ 1];
-  H.psi0 = pd.psi0;
-  mon_load<T>(M, pd.mon, pd.dim);
+__device__ __forceinline__ const ProbHot<T>* hot_table(const LaunchArgs& a);
+template <>
+__device__ __forceinline__ const ProbHot<float>* hot_table<float>(const LaunchArgs& a) {
+  return a.hotf;
+}
+template <>
+__device__ __forceinline__ const ProbHot<double>* hot_table<double>(const LaunchArgs& a) {
+  return a.hotd;
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void load_hdr(const LaunchArgs& a, SmemHdr<T>& S) {
+  // S.w was set by thread 0 and published by a __syncthreads()
+  constexpr int C_SD = (int)(sizeof(SubDesc) / 16), C_PS = (int)(sizeof(ProbState) / 16);
+  coop_copy<NT>(&S.sd, a.subs + S.w.sub, sizeof(SubDesc), 0);
+  coop_copy<NT>(&S.ps, a.st + S.w.prob, sizeof(ProbState), C_SD);
+  coop_copy<NT>(&S.ph, hot_table<T>(a) + S.w.prob, sizeof(ProbHot<T>), C_SD + C_PS);
+}
+
+// q = e / d for 0 <= e < 2^24, 1 <= d < 2^16, via an FP32 reciprocal; the
+// estimate is within one of the quotient and the fix-up makes it exact.
+__device__ __forceinline__ int qdiv(int e, int d, float inv_d) {
+  int q = __float2int_rz(((float)e + 0.5f) * inv_d);
+  const int r = e - q * d;
+  if (r < 0) --q;
+  else if (r >= d) ++q;
+  return q;
 }
 
 // ---------------------------------------------------------------- reductions
@@ -357,253 +335,593 @@ __device__ __forceinline__ void arrive(const LaunchArgs& a, int prob, int ntiles
 
 // ---------------------------------------------------------------- helpers
 // Owner's value at a global node (parallel transmission: previous step).
+// A node outside this subdomain's core along an axis belongs to the
+// neighbouring block on that side (cores hold >= ceil(o/2)+1 nodes).
 template <typename T>
-__device__ __forceinline__ T gather_owner(const LaunchArgs& a, const TileHdr<T>& H, int gi,
-                                          int gj, int gl) {
-  const ProbDesc& pd = a.probs[H.prob];
-  int kx = owner_k(pd.bcore[0], H.parts[0], gi, H.k[0]);
-  int ky = H.dim > 1 ? owner_k(pd.bcore[1], H.parts[1], gj, H.k[1]) : 0;
-  int kz = H.dim > 2 ? owner_k(pd.bcore[2], H.parts[2], gl, H.k[2]) : 0;
-  const SubDesc& od = a.subs[H.sub_base + (kz * H.parts[1] + ky) * H.parts[0] + kx];
-  const T* ov = (const T*)od.v[H.parity];
-  long long li = (long long)(gi - od.g0[0]) +
-                 (long long)od.n[0] * ((gj - od.g0[1]) + (long long)od.n[1] * (gl - od.g0[2]));
-  return ov[li];
+__device__ __forceinline__ T gather_owner(const LaunchArgs& a, const SmemHdr<T>& S, int i, int j,
+                                          int l) {
+  const int kx = S.sd.k[0] + (i < S.sd.clo[0] ? -1 : (i > S.sd.chi[0] ? 1 : 0));
+  const int ky = S.sd.k[1] + (j < S.sd.clo[1] ? -1 : (j > S.sd.chi[1] ? 1 : 0));
+  const int kz = S.sd.k[2] + (l < S.sd.clo[2] ? -1 : (l > S.sd.chi[2] ? 1 : 0));
+  const SubDesc* od = a.subs + S.ph.sub_base + (kz * S.ph.parts[1] + ky) * S.ph.parts[0] + kx;
+  const int ox = S.sd.g0[0] + i - __ldg(&od->g0[0]);
+  const int oy = S.sd.g0[1] + j - __ldg(&od->g0[1]);
+  const int oz = S.sd.g0[2] + l - __ldg(&od->g0[2]);
+  const long long pitch = __ldg(&od->pitch), on1 = __ldg(&od->n[1]);
+  const T* ov = (const T*)od->v[S.ps.parity];
+  return __ldcg(ov + ox + pitch * (oy + on1 * oz));
 }
 
 template <typename T>
-__device__ __forceinline__ T init_value(const TileHdr<T>& H, int gi, int gj, int gl) {
-  if (!H.psi0) return T(0);
-  const long long gflat = (long long)gi + (long long)H.N[0] * (gj + (long long)H.N[1] * gl);
+__device__ __forceinline__ T init_value(const SmemHdr<T>& S, const double* psi0, int gi, int gj,
+                                        int gl) {
+  if (!psi0) return T(0);
+  const long long gflat =
+      (long long)gi + (long long)S.ph.N[0] * (gj + (long long)S.ph.N[1] * gl);
   double q = 0.0;
   const int g[3] = {gi, gj, gl};
   for (int a = 0; a < 3; ++a)
-    if (a < H.dim) {
-      double xi = (double)H.lo[a] + (double)g[a] * H.hd[a];
+    if (a < S.ph.dim) {
+      double xi = (double)S.ph.lo[a] + (double)g[a] * S.ph.hd[a];
       q += 0.5 * xi * xi;
     }
-  return (T)(H.psi0[gflat] - q);
+  return (T)(psi0[gflat] - q);
 }
 
-// Right-hand side at one node from the Hessian entries and mesh point.
-// (The theta^0 pass only needs rho det and a finiteness check, so it uses
-// the log form whatever the right-hand side.)
+// Right-hand side at one node.  The theta^0 pass only needs rho det and a
+// finiteness check, so it uses the log form whatever the right-hand side.
 template <typename T>
-__device__ __forceinline__ T rhs_value(const TileHdr<T>& H, const MonT<T>& M, const T* x, T D,
-                                       T& rho) {
-  rho = rho_at<T>(M, x);
-  if (H.rhs == PMA_RHS_LOG || H.phase != PH_RUN) return Fm<T>::ln(rho * D);
-  const T sc = (H.normalize == PMA_NORM_GLOBAL_THETA) ? H.scale_root : T(1);
-  const T e = T(1) / (T)H.dim;
-  return Fm<T>::pw(sc * rho * D, e) - T(1);
+__device__ __forceinline__ T rhs_value(const SmemHdr<T>& S, int phase, T scale_root, T x0, T x1,
+                                       T x2, T D, T& rho) {
+  rho = rho_at<T>(S.ph.mon, x0, x1, x2);
+  if (S.ph.rhs == PMA_RHS_LOG || phase != PH_RUN) return Fm<T>::ln(rho * D);
+  const T e = T(1) / (T)S.ph.dim;
+  return Fm<T>::pw(scale_root * rho * D, e) - T(1);
 }
 
 template <typename T>
-__device__ __forceinline__ void accumulate(const TileHdr<T>& H, T G, T D, T rho, bool owned,
-                                           int gi, int gj, int gl, int i, int j, int l, T& th,
-                                           T& l2a, T& l2b, T& ws, Acc<T>& acc) {
+__device__ __forceinline__ T trap_t(int gi, int N, T h, T hw) {
+  return (gi == 0 || gi == N - 1) ? hw : h;
+}
+
+template <typename T>
+__device__ __forceinline__ void accumulate(const SmemHdr<T>& S, T G, T D, T rho, bool owned,
+                                           int gi, int gj, int gl, int i, int j, int l, T c_lag,
+                                           T& th, T& l2a, T& l2b, T& ws, Acc<T>& acc) {
   if (!(G == G) || !isfinite(G)) acc.nf += 1;
   acc.gmax = fmax(acc.gmax, G);
   acc.gmin = fmin(acc.gmin, G);
   acc.dmin = fmin(acc.dmin, D);
+  const int dim = S.ph.dim;
   if (owned) {
-    double w = trap_w(gi, H.N[0], H.hd[0]);
-    if (H.dim > 1) w *= trap_w(gj, H.N[1], H.hd[1]);
-    if (H.dim > 2) w *= trap_w(gl, H.N[2], H.hd[2]);
-    th += (T)w * rho * D;
+    T w = trap_t<T>(gi, S.ph.N[0], S.ph.h[0], S.ph.hw[0]) *
+          trap_t<T>(gj, S.ph.N[1], S.ph.h[1], S.ph.hw[1]);
+    if (dim > 2) w *= trap_t<T>(gl, S.ph.N[2], S.ph.h[2], S.ph.hw[2]);
+    th = fma(w, rho * D, th);
   }
-  if (H.stop_norm == PMA_STOP_L2_INCREMENT) {
-    double w = trap_w(i, H.n[0], H.hd[0]);
-    if (H.dim > 1) w *= trap_w(j, H.n[1], H.hd[1]);
-    if (H.dim > 2) w *= trap_w(l, H.n[2], H.hd[2]);
-    T d = G - H.c_lag;
-    l2a += (T)w * d * d;
-    l2b += (T)w * d;
-    ws += (T)w;
+  if (S.ph.stop_norm == PMA_STOP_L2_INCREMENT) {
+    T w = trap_t<T>(i, S.sd.n[0], S.ph.h[0], S.ph.hw[0]) *
+          trap_t<T>(j, S.sd.n[1], S.ph.h[1], S.ph.hw[1]);
+    if (dim > 2) w *= trap_t<T>(l, S.sd.n[2], S.ph.h[2], S.ph.hw[2]);
+    T d = G - c_lag;
+    l2a += w * d * d;
+    l2b += w * d;
+    ws += w;
   }
 }
 
-// ---------------------------------------------------------------- 2D sweep
-template <typename T, int TX, int TY, int RY>
-__global__ void __launch_bounds__(TX * TY / RY) k_sweep2d(LaunchArgs a) {
-  constexpr int NT = TX * TY / RY;
-  constexpr int SX = TX + 2, SY = TY + 2;
-  __shared__ T sv[SY * SX];
-  __shared__ TileHdr<T> H;
-  __shared__ MonT<T> M;
-  __shared__ T red_t[4 * (NT / 32)];
-  __shared__ T red_f[3 * (NT / 32)];
-  __shared__ int red_i[NT / 32];
-  __shared__ int s_last;
-  const int tid = threadIdx.x;
-  const int tx = tid % TX, tyb = tid / TX;
+// ---------------------------------------------------------------- work queue
+// Persistent CTAs pull work items from a per-launch counter; the last CTA
+// to run out resets the counters for the next launch.  The partial record
+// of an item is indexed by the item, so results do not depend on which CTA
+// took it.
+__device__ __forceinline__ int pull_item(const LaunchArgs& a) {
+  return a.t0 + (int)atomicAdd(a.queue, 1u);
+}
+__device__ __forceinline__ void queue_exit(const LaunchArgs& a) {
+  __threadfence();
+  const unsigned int done = atomicAdd(a.queue + 1, 1u);
+  if (done == gridDim.x - 1) {
+    a.queue[0] = 0u;
+    a.queue[1] = 0u;
+    __threadfence();
+  }
+}
 
-  for (int t = a.t0 + blockIdx.x; t < a.t0 + a.nwork; t += gridDim.x) {
-    if (tid == 0) load_header<T>(a, t, H, M);
-    __syncthreads();
-    const int phase = H.phase;
-    if (phase == PH_DONE) {
-      __syncthreads();
-      continue;
+// ---------------------------------------------------------------- vector I/O
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  float v[4];
+  __device__ __forceinline__ void lds(const float* p) {
+    const float4 q = *(const float4*)p;
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+  __device__ __forceinline__ void stg(float* p) const {
+    asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3]));
+  }
+};
+template <>
+struct Vec4<double> {
+  double v[4];
+  __device__ __forceinline__ void lds(const double* p) {
+    const double2 q0 = *(const double2*)p, q1 = *(const double2*)(p + 2);
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+  }
+  __device__ __forceinline__ void stg(double* p) const {
+    asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(v[0]), "d"(v[1]));
+    asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p + 2), "d"(v[2]), "d"(v[3]));
+  }
+};
+
+// 16-byte chunk copy global -> shared (VW elements of T).
+template <typename T>
+__device__ __forceinline__ void copy16(T* d, const T* s) {
+  *(int4*)d = __ldcg((const int4*)s);
+}
+
+// ---------------------------------------------------------------- 2D sweep
+// Shared state of the band kernel: the current and the next work item's
+// descriptors (the next one is fetched with cp.async while the current band
+// is computed), the staged band and the reduction scratch.
+template <typename T>
+using BandHdr = SmemHdr<T>;
+
+template <typename T>
+__device__ __forceinline__ void issue_hdr(const LaunchArgs& a, BandHdr<T>& H, const WorkItem& w) {
+  H.w = w;
+  const char* s0 = (const char*)(a.subs + w.sub);
+  const char* s1 = (const char*)(a.st + w.prob);
+  const char* s2 = (const char*)(hot_table<T>(a) + w.prob);
+  for (int i = 0; i < (int)(sizeof(SubDesc) / 16); ++i) cp_async16((char*)&H.sd + 16 * i, s0 + 16 * i);
+  for (int i = 0; i < (int)(sizeof(ProbState) / 16); ++i) cp_async16((char*)&H.ps + 16 * i, s1 + 16 * i);
+  for (int i = 0; i < (int)(sizeof(ProbHot<T>) / 16); ++i) cp_async16((char*)&H.ph + 16 * i, s2 + 16 * i);
+  cp_async_commit();
+}
+
+// One work item is a band of `rows` x `cols` nodes of one subdomain (cols a
+// multiple of 4 except at the subdomain's right edge; rows padded to a pitch
+// of 4 elements in memory).  Staging (one pass): the band plus a one-node
+// halo goes to shared memory with 16-byte loads, halo columns on the
+// subdomain's x faces take the Neumann mirror, and transmission nodes get
+// the offset correction.  Compute: each thread takes runs of 4 consecutive
+// nodes of a row, reads the 3 x 6 stencil window with aligned vector loads
+// and writes the 4 results with one 16-byte store.  Shared row layout: node
+// column c sits at c + 4 (halo columns at 3 and cols + 4), rows are `SWp`
+// (a multiple of 4) wide.
+template <typename T, int NT, int SMAX>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band2d(LaunchArgs a) {
+  constexpr int VW = 16 / (int)sizeof(T);
+  constexpr int NW = NT / 32;
+  __shared__ __align__(16) T sv[SMAX];
+  __shared__ __align__(16) BandHdr<T> HB[2];
+  __shared__ int s_t[2];
+  __shared__ T red_t[4 * NW];
+  __shared__ T red_f[3 * NW];
+  __shared__ int red_i[NW];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tend = a.t0 + a.nwork;
+  int t_next = 0;
+  WorkItem w_next;
+  if (tid == 0) {
+    const int t0 = pull_item(a);
+    s_t[0] = t0;
+    if (t0 < tend) issue_hdr<T>(a, HB[0], a.work[t0]);
+    t_next = pull_item(a);
+    if (t_next < tend) w_next = a.work[t_next];
+  }
+
+  for (int it = 0;; ++it) {
+    const int b = it & 1;
+    if (tid == 0) cp_async_wait_all();
+    __syncthreads();  // S1: header `b` complete and visible
+    const int t = s_t[b];
+    if (t >= tend) break;
+    if (tid == 0) {
+      // publish and prefetch the following item into the other buffer
+      s_t[b ^ 1] = t_next;
+      if (t_next < tend) {
+        issue_hdr<T>(a, HB[b ^ 1], w_next);
+        t_next = pull_item(a);
+        if (t_next < tend) w_next = a.work[t_next];
+      }
     }
-    const int n0 = H.n[0], n1 = H.n[1];
-    const bool plx = H.faces & 1, phx = H.faces & 2, ply = H.faces & 4, phy = H.faces & 8;
+    BandHdr<T>& H = HB[b];
+    const int phase = H.ps.phase;
+    if (phase == PH_DONE) continue;
+    const int n0 = H.sd.n[0], n1 = H.sd.n[1];
+    const long long pitch = H.sd.pitch;
+    const int i0 = H.w.ij & 0xffff, j0 = H.w.ij >> 16;
+    const int cols = H.w.ext & 0xffff, rows = H.w.ext >> 16;
+    const int faces = H.sd.faces;
+    const int g00 = H.sd.g0[0], g01 = H.sd.g0[1];
+    const T* src = (const T*)H.sd.v[H.ps.parity];
+    T* dst = (T*)H.sd.v[H.ps.parity ^ 1];
+    const int rpr = (cols + 3) >> 2;  // runs per row
+    const int nruns = rows * rpr;
+    const float inv_rpr = 1.0f / (float)rpr;
+    // transmission nodes: local index equal to one of these (-1 = none)
+    const int dlx = (faces & 1) ? -1 : 0, dhx = (faces & 2) ? -1 : n0 - 1;
+    const int dly = (faces & 4) ? -1 : 0, dhy = (faces & 8) ? -1 : n1 - 1;
     T th = 0, l2a = 0, l2b = 0, ws = 0;
     Acc<T> acc{-big_val<T>(), big_val<T>(), big_val<T>(), 0};
 
     if (phase == PH_INIT_V) {
       // v^0 into both buffers (the next pass reads buffer `parity`)
-      for (int r = 0; r < RY; ++r) {
-        const int i = H.x0 + tx, j = H.y0 + tyb * RY + r;
-        if (i < n0 && j < n1) {
-          const T v0 = init_value<T>(H, H.g0[0] + i, H.g0[1] + j, 0);
-          H.dst[(long long)j * n0 + i] = v0;
-          ((T*)H.src)[(long long)j * n0 + i] = v0;
+      const double* psi0 = a.probs[H.w.prob].psi0;
+      const int Nx = H.ph.N[0];
+      for (int q = tid; q < nruns; q += NT) {
+        const int r = qdiv(q, rpr, inv_rpr), c0 = (q - r * rpr) * 4;
+        const int j = j0 + r;
+        Vec4<T> o;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + c0 + u;
+          T v0 = T(0);
+          if (psi0 && i < n0) {
+            const int gi = g00 + i, gj = g01 + j;
+            const double xi = (double)H.ph.lo[0] + (double)gi * H.ph.hd[0];
+            const double et = (double)H.ph.lo[1] + (double)gj * H.ph.hd[1];
+            v0 = (T)(psi0[(long long)gj * Nx + gi] - 0.5 * (xi * xi + et * et));
+          }
+          o.v[u] = v0;
         }
+        o.stg(dst + j * pitch + i0 + c0);
+        o.stg((T*)src + j * pitch + i0 + c0);
       }
     } else {
-      // stage tile + halo of v^n (mirror on Neumann faces)
-      for (int idx = tid; idx < SX * SY; idx += NT) {
-        const int ly = idx / SX, lx = idx - ly * SX;
-        const int i = reflect_clamp(H.x0 - 1 + lx, n0, plx, phx);
-        const int j = reflect_clamp(H.y0 - 1 + ly, n1, ply, phy);
-        T val = H.src[(long long)j * n0 + i];
-        if (is_dir(H.faces, 2, i, j, 0, n0, n1, 1)) val += H.corr;
-        sv[idx] = val;
-      }
-      __syncthreads();
+      const int SWp = ((cols + 3) & ~3) + 8;
+      const int SH = rows + 2;
+      const int cpr = SWp / VW;  // 16-byte chunks per shared row
+      const float inv_cpr = 1.0f / (float)cpr;
+      const bool plx = faces & 1, phx = faces & 2, ply = faces & 4, phy = faces & 8;
+      const T corr = (T)H.ps.corr;
+      // chunks of the band rows (global columns i0-4 .. i0+SWp-5)
+      for (int e = tid; e < SH * cpr; e += NT) {
+        const int r = qdiv(e, cpr, inv_cpr), k = e - r * cpr;
+        const int gs = i0 - 4 + k * VW;
+        if (gs >= 0 && gs + VW <= pitch) {
+          const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
+          T v[VW];
+          *(int4*)v = __ldcg((const int4*)(src + jj * pitch + gs));
+          if (corr != T(0)) {
+            const bool drow = (jj == dly || jj == dhy);
 #pragma unroll
-      for (int r = 0; r < RY; ++r) {
-        const int lyy = tyb * RY + r;
-        const int i = H.x0 + tx, j = H.y0 + lyy;
-        if (i >= n0 || j >= n1) continue;
-        const int gi = H.g0[0] + i, gj = H.g0[1] + j;
-        if (is_dir(H.faces, 2, i, j, 0, n0, n1, 1)) {
-          if (phase == PH_RUN) H.dst[(long long)j * n0 + i] = gather_owner<T>(a, H, gi, gj, 0);
-          continue;
+            for (int q = 0; q < VW; ++q) {
+              const int gc = gs + q;
+              if (drow || ((gc == dlx || gc == dhx) && gc < n0)) v[q] += corr;
+            }
+          }
+          // columns >= n0 are padding or the halo written below: skip them
+          if (gs + VW <= n0) {
+            *(int4*)(sv + r * SWp + k * VW) = *(int4*)v;
+          } else {
+#pragma unroll
+            for (int q = 0; q < VW; ++q)
+              if (gs + q < n0) sv[r * SWp + k * VW + q] = v[q];
+          }
         }
-        const T* c = sv + (lyy + 1) * SX + (tx + 1);
-        const T vc = c[0], ve = c[1], vw = c[-1], vn = c[SX], vs = c[-SX];
-        const T vne = c[SX + 1], vnw = c[SX - 1], vse = c[-SX + 1], vsw = c[-SX - 1];
-        T x[3];
-        x[0] = H.lo[0] + (T)gi * H.h[0] + (ve - vw) * H.inv2h[0];
-        x[1] = H.lo[1] + (T)gj * H.h[1] + (vn - vs) * H.inv2h[1];
-        x[2] = 0;
-        const T hxx = T(1) + (ve - T(2) * vc + vw) * H.invh2[0];
-        const T hyy = T(1) + (vn - T(2) * vc + vs) * H.invh2[1];
-        const T hxy = ((vne - vse) - (vnw - vsw)) * H.inv4hh[0];
-        const T D = hxx * hyy - hxy * hxy;
-        T rho;
-        const T G = rhs_value<T>(H, M, x, D, rho);
-        const bool owned = i >= H.clo[0] && i <= H.chi[0] && j >= H.clo[1] && j <= H.chi[1];
-        accumulate<T>(H, G, D, rho, owned, gi, gj, 0, i, j, 0, th, l2a, l2b, ws, acc);
-        if (phase == PH_RUN) H.dst[(long long)j * n0 + i] = vc + H.dt * (G - H.c_lag);
+      }
+      // halo columns on the subdomain's x faces: mirror (Neumann) or clamp
+      const bool left = (i0 == 0), right = (i0 + cols == n0);
+      if (left || right) {
+        for (int r = tid; r < SH; r += NT) {
+          const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
+          const T cr = (jj == dly || jj == dhy) ? corr : T(0);
+          if (left) sv[r * SWp + 3] = plx ? __ldcg(src + jj * pitch + 1) + cr : T(0);
+          if (right) sv[r * SWp + cols + 4] = phx ? __ldcg(src + jj * pitch + n0 - 2) + cr : T(0);
+        }
+      }
+      __syncthreads();  // S2: band staged
+      const T c_lag = (T)H.ps.c_lag, dt = H.ph.dt;
+      const T scale_root = (T)(H.ph.vol / (T)H.ps.theta_prev);
+      const T inv2h0 = H.ph.inv2h[0], inv2h1 = H.ph.inv2h[1];
+      const T invh20 = H.ph.invh2[0], invh21 = H.ph.invh2[1], inv4 = H.ph.inv4hh[0];
+      const T lo0 = H.ph.lo[0], lo1 = H.ph.lo[1], h0 = H.ph.h[0], h1 = H.ph.h[1];
+      const T hw0 = H.ph.hw[0], hw1 = H.ph.hw[1];
+      const int N0 = H.ph.N[0], N1 = H.ph.N[1];
+      const int clo0 = H.sd.clo[0], chi0 = H.sd.chi[0], clo1 = H.sd.clo[1], chi1 = H.sd.chi[1];
+      const bool want_l2 = H.ph.stop_norm == PMA_STOP_L2_INCREMENT;
+      const bool run = phase == PH_RUN;
+      const bool logrhs = H.ph.rhs == PMA_RHS_LOG || !run;
+      const T inv_dim = T(1) / (T)H.ph.dim;
+      const int mkind = H.ph.mon.kind, nterms = H.ph.mon.nterms;
+      bool fast = (mkind == PMA_MON_SUM);
+      for (int q = 0; q < kMaxTerms; ++q)
+        if (q < nterms && H.ph.mon.t[q].type != PMA_TERM_BUMP && H.ph.mon.t[q].type != PMA_TERM_RING)
+          fast = false;
+
+      for (int q = tid; q < nruns; q += NT) {
+        const int r = qdiv(q, rpr, inv_rpr), c0 = (q - r * rpr) * 4;
+        const int j = j0 + r, gj = g01 + j;
+        const T* p = sv + (r + 1) * SWp + c0 + 4;
+        // 3 x 6 window: columns c0-1 .. c0+4 of rows j-1, j, j+1
+        T wS[6], wC[6], wN[6];
+        {
+          Vec4<T> m;
+          wS[0] = p[-SWp - 1];
+          m.lds(p - SWp);
+          wS[1] = m.v[0]; wS[2] = m.v[1]; wS[3] = m.v[2]; wS[4] = m.v[3];
+          wS[5] = p[-SWp + 4];
+          wC[0] = p[-1];
+          m.lds(p);
+          wC[1] = m.v[0]; wC[2] = m.v[1]; wC[3] = m.v[2]; wC[4] = m.v[3];
+          wC[5] = p[4];
+          wN[0] = p[SWp - 1];
+          m.lds(p + SWp);
+          wN[1] = m.v[0]; wN[2] = m.v[1]; wN[3] = m.v[2]; wN[4] = m.v[3];
+          wN[5] = p[SWp + 4];
+        }
+        const bool rowdir = (j == dly || j == dhy);
+        const bool rowown = (j >= clo1 && j <= chi1);
+        const T wy = (gj == 0 || gj == N1 - 1) ? hw1 : h1;
+        const T wly = (j == 0 || j == n1 - 1) ? hw1 : h1;
+        const T xi1 = fma((T)gj, h1, lo1);
+        T x0[4], x1[4], D[4], rho[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const T vc = wC[u + 1], ve = wC[u + 2], vw = wC[u];
+          const T vn = wN[u + 1], vs = wS[u + 1];
+          const int gi = g00 + i0 + c0 + u;
+          x0[u] = fma((T)gi, h0, lo0) + (ve - vw) * inv2h0;
+          x1[u] = xi1 + (vn - vs) * inv2h1;
+          const T hxx = fma(ve - T(2) * vc + vw, invh20, T(1));
+          const T hyy = fma(vn - T(2) * vc + vs, invh21, T(1));
+          const T hxy = ((wN[u + 2] - wS[u + 2]) - (wN[u] - wS[u])) * inv4;
+          D[u] = fma(hxx, hyy, -hxy * hxy);
+        }
+        if (fast) {
+          const T base = H.ph.mon.base;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) rho[u] = base;
+          for (int k = 0; k < nterms; ++k) {
+            const auto& tm = H.ph.mon.t[k];
+            const T cx = tm.c[0], cy = tm.c[1], r2 = tm.r2, nw = -tm.width, amp = tm.amp;
+            const bool ring = tm.type == PMA_TERM_RING;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const T d0 = x0[u] - cx, d1 = x1[u] - cy;
+              const T qq = fma(d0, d0, d1 * d1);
+              const T s2 = qq - r2;
+              const T uu = ring ? s2 * s2 : qq;
+              rho[u] = fma(amp, Fm<T>::exw(nw * uu), rho[u]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) rho[u] = rho_at<T>(H.ph.mon, x0[u], x1[u], T(0));
+        }
+        Vec4<T> o;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = c0 + u, i = i0 + c;
+          const bool valid = c < cols;
+          const bool dir = rowdir || i == dlx || i == dhx;
+          const T G = logrhs ? Fm<T>::ln(rho[u] * D[u])
+                             : Fm<T>::pw(scale_root * rho[u] * D[u], inv_dim) - T(1);
+          o.v[u] = fma(dt, G - c_lag, wC[u + 1]);
+          if (valid && !dir) {
+            if (!isfinite(G)) acc.nf += 1;
+            acc.gmax = fmax(acc.gmax, G);
+            acc.gmin = fmin(acc.gmin, G);
+            acc.dmin = fmin(acc.dmin, D[u]);
+            const int gi = g00 + i;
+            if (rowown && i >= clo0 && i <= chi0) {
+              const T wx = (gi == 0 || gi == N0 - 1) ? hw0 : h0;
+              th = fma(wx * wy, rho[u] * D[u], th);
+            }
+            if (want_l2) {
+              const T w = ((i == 0 || i == n0 - 1) ? hw0 : h0) * wly;
+              const T d = G - c_lag;
+              l2a = fma(w * d, d, l2a);
+              l2b = fma(w, d, l2b);
+              ws += w;
+            }
+          }
+          if (!valid) o.v[u] = T(0);
+        }
+        if (run) {
+          if (rowdir || (i0 + c0 <= dlx) || (i0 + c0 + 3 >= dhx && dhx >= 0)) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int i = i0 + c0 + u;
+              if (c0 + u < cols && (rowdir || i == dlx || i == dhx))
+                o.v[u] = gather_owner<T>(a, H, i, j, 0);
+            }
+          }
+          o.stg(dst + j * pitch + i0 + c0);
+        }
       }
     }
-    tile_reduce<T, NT>(th, l2a, l2b, ws, acc, a.part + t, H.sub, red_t, red_f, red_i);
-    arrive<NT>(a, H.prob, H.ntiles, phase, &s_last);
+    // tile record and arrival
+    th = warp_sum(th);
+    l2a = warp_sum(l2a);
+    l2b = warp_sum(l2b);
+    ws = warp_sum(ws);
+    const T gmax = warp_max(acc.gmax), gmin = warp_min(acc.gmin), dmin = warp_min(acc.dmin);
+    const int nf = warp_isum(acc.nf);
+    if (lane == 0) {
+      red_t[0 * NW + wid] = th;
+      red_t[1 * NW + wid] = l2a;
+      red_t[2 * NW + wid] = l2b;
+      red_t[3 * NW + wid] = ws;
+      red_f[0 * NW + wid] = gmax;
+      red_f[1 * NW + wid] = gmin;
+      red_f[2 * NW + wid] = dmin;
+      red_i[wid] = nf;
+    }
+    __syncthreads();  // S3
+    if (tid == 0) {
+      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      T m0 = -big_val<T>(), m1 = big_val<T>(), m2 = big_val<T>();
+      int cnt = 0;
+      for (int w = 0; w < NW; ++w) {
+        s0 += red_t[0 * NW + w];
+        s1 += red_t[1 * NW + w];
+        s2 += red_t[2 * NW + w];
+        s3 += red_t[3 * NW + w];
+        m0 = fmax(m0, red_f[0 * NW + w]);
+        m1 = fmin(m1, red_f[1 * NW + w]);
+        m2 = fmin(m2, red_f[2 * NW + w]);
+        cnt += red_i[w];
+      }
+      Partial rec;
+      rec.theta = (double)s0;
+      rec.l2a = (double)s1;
+      rec.l2b = (double)s2;
+      rec.wsum = (double)s3;
+      rec.gmax = (double)m0;
+      rec.gmin = (double)m1;
+      rec.dmin = (double)m2;
+      rec.nonfinite = cnt;
+      rec.sub = H.w.sub;
+      a.part[t] = rec;
+      __threadfence();
+      const unsigned int prev = atomicAdd(&a.st[H.w.prob].tiles_done, 1u);
+      s_last = (prev == (unsigned int)(H.ph.ntiles - 1));
+    }
+    __syncthreads();  // S4
+    if (s_last) {
+      __threadfence();
+      finish_problem<NT>(a, H.w.prob, phase);
+    }
   }
+  if (tid == 0) queue_exit(a);
 }
 
 // ---------------------------------------------------------------- 3D sweep
-// TX x TY threads, each marching TZ planes of the tile.
+// TX x TY threads, each marching up to TZ planes of the tile.
 template <typename T, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(TX * TY) k_sweep3d(LaunchArgs a) {
   constexpr int NT = TX * TY;
   constexpr int SX = TX + 2, SY = TY + 2, SZ = TZ + 2;
-  __shared__ T sv[SZ * SY * SX];
-  __shared__ TileHdr<T> H;
-  __shared__ MonT<T> M;
+  __shared__ __align__(16) T sv[SZ * SY * SX];
+  __shared__ SmemHdr<T> S;
   __shared__ T red_t[4 * (NT / 32)];
   __shared__ T red_f[3 * (NT / 32)];
   __shared__ int red_i[NT / 32];
   __shared__ int s_last;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
+  const int tend = a.t0 + a.nwork;
+  __shared__ int s_t;
+  int nt = 0;
+  WorkItem next;
+  if (tid == 0) {
+    nt = pull_item(a);
+    if (nt < tend) next = a.work[nt];
+  }
 
-  for (int t = a.t0 + blockIdx.x; t < a.t0 + a.nwork; t += gridDim.x) {
-    if (tid == 0) load_header<T>(a, t, H, M);
+  for (;;) {
+    if (tid == 0) {
+      s_t = nt;
+      S.w = next;
+      if (nt < tend) {
+        nt = pull_item(a);
+        if (nt < tend) next = a.work[nt];
+      }
+    }
     __syncthreads();
-    const int phase = H.phase;
+    const int t = s_t;
+    if (t >= tend) break;
+    load_hdr<T, NT>(a, S);
+    __syncthreads();
+    const int phase = S.ps.phase;
     if (phase == PH_DONE) {
       __syncthreads();
       continue;
     }
-    const int n0 = H.n[0], n1 = H.n[1], n2 = H.n[2];
-    const bool plx = H.faces & 1, phx = H.faces & 2, ply = H.faces & 4, phy = H.faces & 8;
-    const bool plz = H.faces & 16, phz = H.faces & 32;
+    const int n0 = S.sd.n[0], n1 = S.sd.n[1], n2 = S.sd.n[2];
+    const int x0 = S.w.ij & 0xffff, y0 = S.w.ij >> 16;
+    const int z0 = S.w.ext & 0xffff, depth = S.w.ext >> 16;
+    const int faces = S.sd.faces;
+    const bool plx = faces & 1, phx = faces & 2, ply = faces & 4, phy = faces & 8;
+    const bool plz = faces & 16, phz = faces & 32;
+    const int g00 = S.sd.g0[0], g01 = S.sd.g0[1], g02 = S.sd.g0[2];
+    const T* src = (const T*)S.sd.v[S.ps.parity];
+    T* dst = (T*)S.sd.v[S.ps.parity ^ 1];
     T th = 0, l2a = 0, l2b = 0, ws = 0;
     Acc<T> acc{-big_val<T>(), big_val<T>(), big_val<T>(), 0};
-    const long long pitch_z = (long long)n0 * n1;
+    const long long rowp = S.sd.pitch;
+    const long long pitch_z = rowp * n1;
+    const int i = x0 + tx, j = y0 + ty;
 
     if (phase == PH_INIT_V) {
-      for (int r = 0; r < TZ; ++r) {
-        const int i = H.x0 + tx, j = H.y0 + ty, l = H.z0 + r;
+      const double* psi0 = a.probs[S.w.prob].psi0;
+      for (int r = 0; r < depth; ++r) {
+        const int l = z0 + r;
         if (i < n0 && j < n1 && l < n2) {
-          const T v0 = init_value<T>(H, H.g0[0] + i, H.g0[1] + j, H.g0[2] + l);
-          H.dst[l * pitch_z + (long long)j * n0 + i] = v0;
-          ((T*)H.src)[l * pitch_z + (long long)j * n0 + i] = v0;
+          const T v0 = init_value<T>(S, psi0, g00 + i, g01 + j, g02 + l);
+          st_global(dst + l * pitch_z + j * rowp + i, v0);
+          st_global((T*)src + l * pitch_z + j * rowp + i, v0);
         }
       }
     } else {
-      for (int idx = tid; idx < SX * SY * SZ; idx += NT) {
+      const T corr = (T)S.ps.corr;
+      const int SZa = depth + 2;
+      for (int idx = tid; idx < SX * SY * SZa; idx += NT) {
         const int lz = idx / (SX * SY);
         const int rem = idx - lz * SX * SY;
         const int ly = rem / SX, lx = rem - ly * SX;
-        const int i = reflect_clamp(H.x0 - 1 + lx, n0, plx, phx);
-        const int j = reflect_clamp(H.y0 - 1 + ly, n1, ply, phy);
-        const int l = reflect_clamp(H.z0 - 1 + lz, n2, plz, phz);
-        T val = H.src[l * pitch_z + (long long)j * n0 + i];
-        if (is_dir(H.faces, 3, i, j, l, n0, n1, n2)) val += H.corr;
+        const int ii = reflect_clamp(x0 - 1 + lx, n0, plx, phx);
+        const int jj = reflect_clamp(y0 - 1 + ly, n1, ply, phy);
+        const int ll = reflect_clamp(z0 - 1 + lz, n2, plz, phz);
+        T val = __ldcg(src + ll * pitch_z + jj * rowp + ii);
+        if (is_dir(faces, 3, ii, jj, ll, n0, n1, n2)) val += corr;
         sv[idx] = val;
       }
       __syncthreads();
-      const int i = H.x0 + tx, j = H.y0 + ty;
-      for (int r = 0; r < TZ; ++r) {
-        const int l = H.z0 + r;
+      const T c_lag = (T)S.ps.c_lag, dt = S.ph.dt;
+      const T scale_root = (T)(S.ph.vol / (T)S.ps.theta_prev);
+      for (int r = 0; r < depth; ++r) {
+        const int l = z0 + r;
         if (i >= n0 || j >= n1 || l >= n2) continue;
-        const int gi = H.g0[0] + i, gj = H.g0[1] + j, gl = H.g0[2] + l;
-        const long long gidx = l * pitch_z + (long long)j * n0 + i;
-        if (is_dir(H.faces, 3, i, j, l, n0, n1, n2)) {
-          if (phase == PH_RUN) H.dst[gidx] = gather_owner<T>(a, H, gi, gj, gl);
+        const int gi = g00 + i, gj = g01 + j, gl = g02 + l;
+        const long long gidx = l * pitch_z + j * rowp + i;
+        if (is_dir(faces, 3, i, j, l, n0, n1, n2)) {
+          if (phase == PH_RUN) st_global(dst + gidx, gather_owner<T>(a, S, i, j, l));
           continue;
         }
         const T* c = sv + ((r + 1) * SY + (ty + 1)) * SX + (tx + 1);
         constexpr int PY = SX, PZ = SX * SY;
         const T vc = c[0];
         const T vxp = c[1], vxm = c[-1], vyp = c[PY], vym = c[-PY], vzp = c[PZ], vzm = c[-PZ];
-        T x[3];
-        x[0] = H.lo[0] + (T)gi * H.h[0] + (vxp - vxm) * H.inv2h[0];
-        x[1] = H.lo[1] + (T)gj * H.h[1] + (vyp - vym) * H.inv2h[1];
-        x[2] = H.lo[2] + (T)gl * H.h[2] + (vzp - vzm) * H.inv2h[2];
-        const T hxx = T(1) + (vxp - T(2) * vc + vxm) * H.invh2[0];
-        const T hyy = T(1) + (vyp - T(2) * vc + vym) * H.invh2[1];
-        const T hzz = T(1) + (vzp - T(2) * vc + vzm) * H.invh2[2];
-        const T hxy = ((c[PY + 1] - c[-PY + 1]) - (c[PY - 1] - c[-PY - 1])) * H.inv4hh[0];
-        const T hxz = ((c[PZ + 1] - c[-PZ + 1]) - (c[PZ - 1] - c[-PZ - 1])) * H.inv4hh[1];
-        const T hyz = ((c[PZ + PY] - c[-PZ + PY]) - (c[PZ - PY] - c[-PZ - PY])) * H.inv4hh[2];
+        const T xx = fma((T)gi, S.ph.h[0], S.ph.lo[0]) + (vxp - vxm) * S.ph.inv2h[0];
+        const T xy = fma((T)gj, S.ph.h[1], S.ph.lo[1]) + (vyp - vym) * S.ph.inv2h[1];
+        const T xz = fma((T)gl, S.ph.h[2], S.ph.lo[2]) + (vzp - vzm) * S.ph.inv2h[2];
+        const T hxx = T(1) + (vxp - T(2) * vc + vxm) * S.ph.invh2[0];
+        const T hyy = T(1) + (vyp - T(2) * vc + vym) * S.ph.invh2[1];
+        const T hzz = T(1) + (vzp - T(2) * vc + vzm) * S.ph.invh2[2];
+        const T hxy = ((c[PY + 1] - c[-PY + 1]) - (c[PY - 1] - c[-PY - 1])) * S.ph.inv4hh[0];
+        const T hxz = ((c[PZ + 1] - c[-PZ + 1]) - (c[PZ - 1] - c[-PZ - 1])) * S.ph.inv4hh[1];
+        const T hyz = ((c[PZ + PY] - c[-PZ + PY]) - (c[PZ - PY] - c[-PZ - PY])) * S.ph.inv4hh[2];
         const T D = hxx * (hyy * hzz - hyz * hyz) - hxy * (hxy * hzz - hyz * hxz) +
                     hxz * (hxy * hyz - hyy * hxz);
         T rho;
-        const T G = rhs_value<T>(H, M, x, D, rho);
-        const bool owned = i >= H.clo[0] && i <= H.chi[0] && j >= H.clo[1] && j <= H.chi[1] &&
-                           l >= H.clo[2] && l <= H.chi[2];
-        accumulate<T>(H, G, D, rho, owned, gi, gj, gl, i, j, l, th, l2a, l2b, ws, acc);
-        if (phase == PH_RUN) H.dst[gidx] = vc + H.dt * (G - H.c_lag);
+        const T G = rhs_value<T>(S, phase, scale_root, xx, xy, xz, D, rho);
+        const bool owned = i >= S.sd.clo[0] && i <= S.sd.chi[0] && j >= S.sd.clo[1] &&
+                           j <= S.sd.chi[1] && l >= S.sd.clo[2] && l <= S.sd.chi[2];
+        accumulate<T>(S, G, D, rho, owned, gi, gj, gl, i, j, l, c_lag, th, l2a, l2b, ws, acc);
+        if (phase == PH_RUN) st_global(dst + gidx, fma(dt, G - c_lag, vc));
       }
     }
-    tile_reduce<T, NT>(th, l2a, l2b, ws, acc, a.part + t, H.sub, red_t, red_f, red_i);
-    arrive<NT>(a, H.prob, H.ntiles, phase, &s_last);
+    tile_reduce<T, NT>(th, l2a, l2b, ws, acc, a.part + t, S.w.sub, red_t, red_f, red_i);
+    arrive<NT>(a, S.w.prob, S.ph.ntiles, phase, &s_last);
   }
+  if (tid == 0) queue_exit(a);
 }
 
 // ---------------------------------------------------------------- dispatch
-// Compiled tile shapes.  2D: (TX, TY, RY); 3D: (TX, TY, TZ).
-#define PMA_T2D(X) X(32, 16, 2) X(32, 8, 1) X(64, 8, 2) X(16, 16, 2)
+// Compiled shapes.  2D: (threads, band nodes FP32, band nodes FP64); the
+// staged band plus halo is at most 3x the band nodes.  3D: (TX, TY, TZ).
+#define PMA_T2D(X) X(256, 2048, 1024) X(128, 1024, 512) X(256, 1024, 1024) X(512, 3072, 1536)
 #define PMA_T3D(X) X(32, 8, 4) X(32, 4, 8) X(16, 8, 8)
 
-static const Tile2D k_t2d[] = {
-#define E(a, b, c) {a, b},
+static const int k_t2d[][3] = {
+#define E(a, b, c) {a, b, c},
     PMA_T2D(E)
 #undef E
 };
@@ -615,17 +933,28 @@ static const Tile3D k_t3d[] = {
 
 int tile2d_count() { return (int)(sizeof(k_t2d) / sizeof(k_t2d[0])); }
 int tile3d_count() { return (int)(sizeof(k_t3d) / sizeof(k_t3d[0])); }
-Tile2D tile2d_shape(int id) { return k_t2d[id]; }
+Tile2D tile2d_shape(int id, bool fp64) {
+  Tile2D t;
+  t.threads = k_t2d[id][0];
+  t.nodes = fp64 ? k_t2d[id][2] : k_t2d[id][1];
+  t.smax = 3 * t.nodes;
+  // a one-row band plus halo must fit: 3 * (cols + 8) <= smax, cols % 4 == 0
+  t.cols = ((t.smax / 3 - 8) & ~3) < 1024 ? ((t.smax / 3 - 8) & ~3) : 1024;
+  return t;
+}
 Tile3D tile3d_shape(int id) { return k_t3d[id]; }
 
 template <typename T>
 static const void* sweep_fn(int dim, int id, int* nthreads) {
   int k = 0;
   if (dim == 2) {
-#define E(a, b, c)                                   \
-  if (k++ == id) {                                   \
-    *nthreads = (a) * (b) / (c);                     \
-    return (const void*)k_sweep2d<T, a, b, c>;       \
+#define E(a, b, c)                                                         \
+  if (k++ == id) {                                                         \
+    *nthreads = (a);                                                       \
+    if constexpr (sizeof(T) == 8)                                          \
+      return (const void*)k_band2d<T, a, 3 * (c)>;                         \
+    else                                                                   \
+      return (const void*)k_band2d<T, a, 3 * (b)>;                         \
   }
     PMA_T2D(E)
 #undef E
@@ -680,7 +1009,7 @@ __device__ __forceinline__ T fetch_v(const SubDesc& sd, const T* v, int dim, int
   i = reflect_clamp(i, n0, sd.faces & 1, sd.faces & 2);
   j = dim > 1 ? reflect_clamp(j, n1, sd.faces & 4, sd.faces & 8) : 0;
   l = dim > 2 ? reflect_clamp(l, n2, sd.faces & 16, sd.faces & 32) : 0;
-  T val = v[(long long)i + (long long)n0 * (j + (long long)n1 * l)];
+  T val = v[(long long)i + (long long)sd.pitch * (j + (long long)n1 * l)];
   if (is_dir(sd.faces, dim, i, j, l, n0, n1, n2)) val += (T)corr;
   return val;
 }
@@ -721,7 +1050,7 @@ __device__ void combine_node(const CombineJob& J, long long g, const SubDesc* su
       ((float*)J.x)[a * N + g] = (float)xa;
   }
   if (J.psi) {
-    const double vv = (double)v[(long long)i + (long long)sd.n[0] * (j + (long long)sd.n[1] * l)];
+    const double vv = (double)v[(long long)i + (long long)sd.pitch * (j + (long long)sd.n[1] * l)];
     const double psi = vv - ps.shift + q;
     if (J.out_fp64)
       ((double*)J.psi)[g] = psi;

@@ -92,6 +92,13 @@ class pma_info(C.Structure):
                 ("reserved", C.c_int32), ("latency_us", C.c_double)]
 
 
+class pma_stats(C.Structure):
+    _fields_ = [("windows", C.c_int64), ("sweep_launches", C.c_int64),
+                ("other_launches", C.c_int64), ("node_updates", C.c_int64),
+                ("sweep_bytes", C.c_double), ("window_ms", C.c_double),
+                ("h2d_bytes", C.c_double), ("d2h_bytes", C.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -110,6 +117,10 @@ _SIGS = {
     "pma_run": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int32)]),
     "pma_serve_start": (C.c_int, [C.c_void_p]),
     "pma_serve_stop": (C.c_int, [C.c_void_p]),
+    "pma_admit": (C.c_int, [C.c_void_p]),
+    "pma_get_mesh_device_batch": (C.c_int, [C.c_void_p, C.c_int32, _P(C.c_uint64),
+                                            _P(C.c_void_p), C.c_int32]),
+    "pma_get_stats": (C.c_int, [C.c_void_p, _P(pma_stats), C.c_int32]),
     "pma_poll": (C.c_int, [C.c_void_p, C.c_uint64, _P(C.c_int32)]),
     "pma_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64]),
     "pma_get_mesh": (C.c_int, [C.c_void_p, C.c_uint64, _P(C.c_double), _P(C.c_double),
@@ -117,6 +128,7 @@ _SIGS = {
     "pma_get_mesh_device": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int32,
                                       C.c_void_p, _P(pma_info)]),
     "pma_check_mesh": (C.c_int, [C.c_void_p, C.c_uint64, _P(C.c_double)]),
+    "pma_get_info": (C.c_int, [C.c_void_p, C.c_uint64, _P(pma_info)]),
     "pma_release": (C.c_int, [C.c_void_p, C.c_uint64]),
     "pma_counts": (C.c_int, [C.c_void_p, _P(C.c_int32), _P(C.c_int32), _P(C.c_int32)]),
     "pma_solve": (C.c_int, [C.c_int, _P(pma_grid), _P(pma_monitor), _P(pma_decomp),
@@ -211,6 +223,24 @@ def pma_serve_stop(ctx) -> int:
     return _call("pma_serve_stop", ctx)
 
 
+def pma_admit(ctx) -> int:
+    return _call("pma_admit", ctx)
+
+
+def pma_get_mesh_device_batch(ctx, ids: Sequence[int], x_dev_ptrs: Sequence[int],
+                              out_fp64: int = 1) -> int:
+    n = len(ids)
+    a = (C.c_uint64 * max(n, 1))(*ids)
+    b = (C.c_void_p * max(n, 1))(*[C.c_void_p(p) for p in x_dev_ptrs])
+    return _call("pma_get_mesh_device_batch", ctx, n, a, b, out_fp64)
+
+
+def pma_get_stats(ctx, reset: int = 0):
+    s = pma_stats()
+    st = _call("pma_get_stats", ctx, C.byref(s), reset)
+    return st, s
+
+
 def pma_poll(ctx, rid: int):
     d = C.c_int32()
     st = _call("pma_poll", ctx, rid, C.byref(d))
@@ -246,6 +276,12 @@ def pma_check_mesh(ctx, rid: int):
     out = (C.c_double * 4)()
     st = _call("pma_check_mesh", ctx, rid, out)
     return st, list(out)
+
+
+def pma_get_info(ctx, rid: int):
+    info = pma_info()
+    st = _call("pma_get_info", ctx, rid, C.byref(info))
+    return st, info
 
 
 def pma_release(ctx, rid: int) -> int:
