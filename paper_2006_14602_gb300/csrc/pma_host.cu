@@ -243,6 +243,10 @@ struct pma_ctx {
   Partial* d_part[NUM_CLS] = {};
   size_t work_cap[NUM_CLS] = {};
   int nwork[NUM_CLS] = {};
+  int* d_fin[NUM_CLS] = {};           // live problem slots per class
+  size_t fin_cap[NUM_CLS] = {};
+  int nfin[NUM_CLS] = {};
+  std::vector<int> h_fin[NUM_CLS];
   unsigned int* d_queue = nullptr;  // 2 counters per class
   int grid[NUM_CLS] = {};
   int tile_id[NUM_CLS] = {};
@@ -428,6 +432,7 @@ pma_status rebuild(pma_ctx* c) {
   c->h_subs.clear();
   for (int k = 0; k < NUM_CLS; ++k) {
     c->h_work[k].clear();
+    c->h_fin[k].clear();
     c->tile_id[k] = pick_tile(c, k);
   }
   c->live_tiles = 0;
@@ -468,7 +473,7 @@ pma_status rebuild(pma_ctx* c) {
             const int cols = std::min(t2.cols, hs.n[0] - x);
             const int swp = ((cols + 3) & ~3) + 8;
             int rows = std::max(1, std::min(hs.n[1], t2.nodes / ((cols + 3) & ~3)));
-            while (rows > 1 && (rows + 2) * swp > t2.smax) --rows;
+            while (rows > 1 && ((rows + 2) * swp > t2.smax || rows + 2 > 2 * t2.threads)) --rows;
             for (int y = 0; y < hs.n[1]; y += rows) {
               const int rr = std::min(rows, hs.n[1] - y);
               wl.push_back(WorkItem{sidx, r.slot, x | (y << 16), cols | (rr << 16)});
@@ -487,7 +492,10 @@ pma_status rebuild(pma_ctx* c) {
       c->h_subs.push_back(sd);
     }
     pd.tile_end = (int)wl.size();
-    if (live) c->live_tiles += pd.tile_end - pd.tile_begin;
+    if (live) {
+      c->live_tiles += pd.tile_end - pd.tile_begin;
+      c->h_fin[r.cls].push_back(r.slot);
+    }
     fill_hot<float>(r, pd, c->h_hotf[r.slot]);
     fill_hot<double>(r, pd, c->h_hotd[r.slot]);
   }
@@ -506,6 +514,12 @@ pma_status rebuild(pma_ctx* c) {
       PMA_CK(cudaMalloc(&c->d_part[k], sizeof(Partial) * c->work_cap[k]));
     }
     c->nwork[k] = (int)c->h_work[k].size();
+    c->nfin[k] = (int)c->h_fin[k].size();
+    if ((st = ensure_buf(&c->d_fin[k], &c->fin_cap[k], c->h_fin[k].size() + 1)) != PMA_OK)
+      return st;
+    if (c->nfin[k])
+      PMA_CK(cudaMemcpyAsync(c->d_fin[k], c->h_fin[k].data(), sizeof(int) * c->nfin[k],
+                             cudaMemcpyHostToDevice, c->stream));
     if (c->nwork[k])
       PMA_CK(cudaMemcpyAsync(c->d_work[k], c->h_work[k].data(),
                              sizeof(WorkItem) * c->nwork[k], cudaMemcpyHostToDevice,
@@ -560,6 +574,8 @@ pma_status launch_step(pma_ctx* c) {
       LaunchArgs a = args_for(c, k, 0, c->nwork[k]);
       PMA_CK(launch_sweep(k, c->tile_id[k], a, c->stream));
     }
+    PMA_CK(launch_finish(c->d_fin[k], c->nfin[k], c->d_subs, c->d_probs, c->d_state,
+                         c->d_part[k], c->stream));
   }
   return PMA_OK;
 }
@@ -574,6 +590,7 @@ int launches_per_step(pma_ctx* c) {
     } else {
       ++n;
     }
+    ++n;  // finish
   }
   return n;
 }
@@ -837,6 +854,7 @@ pma_status pma_destroy(pma_ctx* c) {
   for (int k = 0; k < NUM_CLS; ++k) {
     cudaFree(c->d_work[k]);
     cudaFree(c->d_part[k]);
+    cudaFree(c->d_fin[k]);
   }
   cudaFree(c->d_jobs);
   cudaFree(c->d_check);

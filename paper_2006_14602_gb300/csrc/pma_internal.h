@@ -168,6 +168,11 @@ Tile3D tile3d_shape(int id);
 cudaError_t launch_sweep(int cls, int tile_id, const LaunchArgs& a, cudaStream_t s);
 int sweep_max_blocks_per_sm(int cls, int tile_id);
 
+// After a sweep launch: fold the tile records of the listed problem slots
+// (one warp each) and advance their scalars.
+cudaError_t launch_finish(const int* list, int n, const SubDesc* subs, const ProbDesc* probs,
+                          ProbState* st, const Partial* part, cudaStream_t s);
+
 struct CombineJob {
   int prob;        // slot
   int out_fp64;

@@ -163,77 +163,65 @@ __device__ __forceinline__ void tile_reduce(T th, T l2a, T l2b, T ws, Acc<T> acc
   }
 }
 
-// Fold the partial records of problem p (run by the last block to arrive).
-template <int NT>
-__device__ void finish_problem(const LaunchArgs& a, int p, int phase) {
-  constexpr int NW = NT / 32;
-  __shared__ double s_d[NW];
-  __shared__ double s_f[NW];
-  __shared__ int s_i[NW];
-  __shared__ double s_r[NW];
-  __shared__ double s_c;
-  const ProbDesc& pd = a.probs[p];
-  ProbState* ps = a.st + p;
+// ---------------------------------------------------------------- finish
+// After each sweep launch: one warp per problem folds the problem's tile
+// records in a fixed order (lane l takes records l, l+32, ...; xor-tree
+// reductions), so the result is bitwise independent of how the sweep was
+// scheduled.  It derives theta^n and c^n = log(theta^n/|Omega_c|) (the
+// normalised density of Eq. edp), the residual of the stop rule
+// (Eq. dd_stop_criterion; Algorithm 1 steps 5-6), checks for tangling, and
+// advances the problem's scalars.
+__device__ __forceinline__ double warp_dsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void k_finish(const int* __restrict__ list, int n, const SubDesc* __restrict__ subs,
+                         const ProbDesc* __restrict__ probs, ProbState* st,
+                         const Partial* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n) return;
+  const int p = list[w];
+  ProbState* ps = st + p;
+  const int phase = ps->phase;
+  if (phase == PH_DONE) return;
+  const ProbDesc& pd = probs[p];
   const int tb = pd.tile_begin, te = pd.tile_end;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-
-  // pass 1: theta (fixed-order sum), non-finite count, min det
-  double th = 0.0;
-  double dmin = DBL_MAX;
-  int nf = 0;
-  for (int t = tb + threadIdx.x; t < te; t += NT) {
-    const Partial* q = a.part + t;
-    th += __ldcg(&q->theta);
-    dmin = fmin(dmin, __ldcg(&q->dmin));
-    nf += __ldcg(&q->nonfinite);
-  }
-  th = warp_sum(th);
-  dmin = warp_min(dmin);
-  nf = warp_isum(nf);
-  if (lane == 0) {
-    s_d[wid] = th;
-    s_f[wid] = dmin;
-    s_i[wid] = nf;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double T0 = 0.0;
-    double dm = DBL_MAX;
-    int n = 0;
-    for (int w = 0; w < NW; ++w) {
-      T0 += s_d[w];
-      dm = fmin(dm, s_f[w]);
-      n += s_i[w];
-    }
-    s_d[0] = T0;
-    s_f[0] = dm;
-    s_i[0] = n;
-    double c = 0.0;
-    if (pd.rhs == PMA_RHS_LOG && pd.normalize == PMA_NORM_GLOBAL_THETA) c = log(T0 / pd.vol);
-    s_c = c;
-  }
-  __syncthreads();
-  const double theta = s_d[0];
-  const double dmin_all = s_f[0];
-  const int nf_all = s_i[0];
-  const double c_n = s_c;
-
   if (phase == PH_INIT_V) {
-    if (threadIdx.x == 0) {
-      ps->phase = PH_INIT_THETA;
-      ps->tiles_done = 0;
-    }
+    if (lane == 0) ps->phase = PH_INIT_THETA;
     return;
   }
-  const bool tangled = nf_all > 0 || !(dmin_all > 0.0) || !isfinite(theta);
+  const double c_lag = ps->c_lag;
+  // pass 1: theta, extrema of G, min det, non-finite count
+  double th = 0.0, gx = -DBL_MAX, gn = DBL_MAX, dm = DBL_MAX;
+  int nf = 0;
+  for (int t = tb + lane; t < te; t += 32) {
+    const Partial& q = part[t];
+    th += q.theta;
+    gx = fmax(gx, q.gmax);
+    gn = fmin(gn, q.gmin);
+    dm = fmin(dm, q.dmin);
+    nf += q.nonfinite;
+  }
+  th = warp_dsum(th);
+  gx = warp_max(gx);
+  gn = warp_min(gn);
+  dm = warp_min(dm);
+  nf = warp_isum(nf);
+  const double theta = th;
+  double c_n = 0.0;
+  if (pd.rhs == PMA_RHS_LOG && pd.normalize == PMA_NORM_GLOBAL_THETA) c_n = log(theta / pd.vol);
+  const bool tangled = nf > 0 || !(dm > 0.0) || !isfinite(theta);
   if (phase == PH_INIT_THETA) {
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
       ps->theta = theta;
       ps->theta_prev = theta;
       ps->c_lag = c_n;
       ps->corr = 0.0;
       ps->shift = 0.0;
-      ps->min_det = dmin_all;
+      ps->min_det = dm;
       if (tangled) {
         ps->status = PMA_ERR_TANGLED;
         ps->phase = PH_DONE;
@@ -243,52 +231,49 @@ __device__ void finish_problem(const LaunchArgs& a, int p, int phase) {
       } else {
         ps->phase = PH_RUN;
       }
-      ps->tiles_done = 0;
     }
     return;
   }
-
-  // pass 2: residual per subdomain (one warp per subdomain), then over
-  // subdomains by the stop rule (max = ALL, min = ANY)
+  // residual: per subdomain, combined by the stop rule (max = ALL, min = ANY)
   const bool any = (pd.stop_rule == PMA_RULE_ANY);
-  const double c_lag = ps->c_lag;
-  const double delta = c_n - c_lag;
-  double r_w = any ? INFINITY : 0.0;
-  for (int s = wid; s < pd.nsub; s += NW) {
-    const SubDesc& sd = a.subs[pd.sub_base + s];
-    double r_s;
-    if (pd.stop_norm == PMA_STOP_MAX_UT) {
-      double gx = -DBL_MAX, gn = DBL_MAX;
-      for (int t = sd.tile_begin + lane; t < sd.tile_end; t += 32) {
-        gx = fmax(gx, __ldcg(&a.part[t].gmax));
-        gn = fmin(gn, __ldcg(&a.part[t].gmin));
+  double r;
+  if (pd.stop_norm == PMA_STOP_MAX_UT && !any) {
+    r = fmax(gx - c_n, c_n - gn);
+  } else {
+    const double delta = c_n - c_lag;
+    r = any ? INFINITY : 0.0;
+    for (int s = 0; s < pd.nsub; ++s) {
+      const SubDesc& sd = subs[pd.sub_base + s];
+      double r_s;
+      if (pd.stop_norm == PMA_STOP_MAX_UT) {
+        double a1 = -DBL_MAX, a2 = DBL_MAX;
+        for (int t = sd.tile_begin + lane; t < sd.tile_end; t += 32) {
+          a1 = fmax(a1, part[t].gmax);
+          a2 = fmin(a2, part[t].gmin);
+        }
+        a1 = warp_max(a1);
+        a2 = warp_min(a2);
+        r_s = fmax(a1 - c_n, c_n - a2);
+      } else {
+        double A = 0.0, B = 0.0, W = 0.0;
+        for (int t = sd.tile_begin + lane; t < sd.tile_end; t += 32) {
+          A += part[t].l2a;
+          B += part[t].l2b;
+          W += part[t].wsum;
+        }
+        A = warp_dsum(A);
+        B = warp_dsum(B);
+        W = warp_dsum(W);
+        // sum w (G - c_n)^2 = sum w (G - c_lag - delta)^2
+        const double q = A - 2.0 * delta * B + delta * delta * W;
+        r_s = pd.dt * sqrt(q > 0.0 ? q : 0.0);
       }
-      gx = warp_max(gx);
-      gn = warp_min(gn);
-      r_s = fmax(gx - c_n, c_n - gn);
-    } else {
-      double A = 0.0, B = 0.0, W = 0.0;
-      for (int t = sd.tile_begin + lane; t < sd.tile_end; t += 32) {
-        A += __ldcg(&a.part[t].l2a);
-        B += __ldcg(&a.part[t].l2b);
-        W += __ldcg(&a.part[t].wsum);
-      }
-      A = warp_sum(A);
-      B = warp_sum(B);
-      W = warp_sum(W);
-      // sum w (G - c_n)^2 = sum w (G - c_lag - delta)^2
-      double q = A - 2.0 * delta * B + delta * delta * W;
-      r_s = pd.dt * sqrt(q > 0.0 ? q : 0.0);
+      r = any ? fmin(r, r_s) : fmax(r, r_s);
     }
-    r_w = any ? fmin(r_w, r_s) : fmax(r_w, r_s);
   }
-  if (lane == 0) s_r[wid] = r_w;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double r = any ? INFINITY : 0.0;
-    for (int w = 0; w < NW; ++w) r = any ? fmin(r, s_r[w]) : fmax(r, s_r[w]);
+  if (lane == 0) {
     ps->theta = theta;
-    ps->min_det = dmin_all;
+    ps->min_det = dm;
     if (tangled) {
       ps->status = PMA_ERR_TANGLED;
       ps->phase = PH_DONE;
@@ -301,7 +286,7 @@ __device__ void finish_problem(const LaunchArgs& a, int p, int phase) {
       ps->c_lag = c_n;
       ps->theta_prev = theta;
       ps->parity ^= 1;
-      long long step = ps->step + 1;
+      const long long step = ps->step + 1;
       ps->step = step;
       if ((step % pd.check_every) == 0 && r <= pd.tol) {
         ps->status = PMA_OK;
@@ -311,26 +296,16 @@ __device__ void finish_problem(const LaunchArgs& a, int p, int phase) {
         ps->phase = PH_DONE;
       }
     }
-    ps->tiles_done = 0;
   }
 }
 
-// Arrival: publish this tile's record, elect the last tile of the problem.
-template <int NT>
-__device__ __forceinline__ void arrive(const LaunchArgs& a, int prob, int ntiles, int phase,
-                                       int* s_last) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned int prev = atomicAdd(&a.st[prob].tiles_done, 1u);
-    *s_last = (prev == (unsigned int)(ntiles - 1));
-  }
-  __syncthreads();
-  if (*s_last) {
-    __threadfence();
-    finish_problem<NT>(a, prob, phase);
-  }
-  __syncthreads();
+cudaError_t launch_finish(const int* list, int n, const SubDesc* subs, const ProbDesc* probs,
+                          ProbState* st, const Partial* part, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int threads = 128;
+  const int blocks = (n * 32 + threads - 1) / threads;
+  k_finish<<<blocks, threads, 0, s>>>(list, n, subs, probs, st, part);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- helpers
@@ -501,7 +476,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
   __shared__ T red_t[4 * NW];
   __shared__ T red_f[3 * NW];
   __shared__ int red_i[NW];
-  __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int tend = a.t0 + a.nwork;
   int t_next = 0;
@@ -578,41 +552,72 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
       const int cpr = SWp / VW;  // 16-byte chunks per shared row
       const float inv_cpr = 1.0f / (float)cpr;
       const bool plx = faces & 1, phx = faces & 2, ply = faces & 4, phy = faces & 8;
-      const T corr = (T)H.ps.corr;
-      // chunks of the band rows (global columns i0-4 .. i0+SWp-5)
+      // (a) 16-byte asynchronous copies of the band rows (global columns
+      //     i0-4 .. i0+SWp-5; chunks outside the pitched row are skipped)
       for (int e = tid; e < SH * cpr; e += NT) {
         const int r = qdiv(e, cpr, inv_cpr), k = e - r * cpr;
         const int gs = i0 - 4 + k * VW;
         if (gs >= 0 && gs + VW <= pitch) {
           const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
-          T v[VW];
-          *(int4*)v = __ldcg((const int4*)(src + jj * pitch + gs));
-          if (corr != T(0)) {
-            const bool drow = (jj == dly || jj == dhy);
-#pragma unroll
-            for (int q = 0; q < VW; ++q) {
-              const int gc = gs + q;
-              if (drow || ((gc == dlx || gc == dhx) && gc < n0)) v[q] += corr;
-            }
-          }
-          // columns >= n0 are padding or the halo written below: skip them
-          if (gs + VW <= n0) {
-            *(int4*)(sv + r * SWp + k * VW) = *(int4*)v;
-          } else {
-#pragma unroll
-            for (int q = 0; q < VW; ++q)
-              if (gs + q < n0) sv[r * SWp + k * VW + q] = v[q];
-          }
+          cp_async16(sv + r * SWp + k * VW, src + jj * pitch + gs);
         }
       }
-      // halo columns on the subdomain's x faces: mirror (Neumann) or clamp
+      cp_async_commit();
+      // (b) halo columns on the subdomain's x faces (Neumann mirror; clamp on
+      //     transmission faces, where the value is never used): loaded now,
+      //     written after the copies land.  At most 2 rows per thread.
       const bool left = (i0 == 0), right = (i0 + cols == n0);
-      if (left || right) {
-        for (int r = tid; r < SH; r += NT) {
+      const T corr = (T)H.ps.corr;
+      T hl[2], hr[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int r = tid + q * NT;
+        hl[q] = hr[q] = T(0);
+        if (r < SH && (left || right)) {
           const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
           const T cr = (jj == dly || jj == dhy) ? corr : T(0);
-          if (left) sv[r * SWp + 3] = plx ? __ldcg(src + jj * pitch + 1) + cr : T(0);
-          if (right) sv[r * SWp + cols + 4] = phx ? __ldcg(src + jj * pitch + n0 - 2) + cr : T(0);
+          if (left && plx) hl[q] = __ldcg(src + jj * pitch + 1) + cr;
+          if (right && phx) hr[q] = __ldcg(src + jj * pitch + n0 - 2) + cr;
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      // (c) halo values, and the offset of transmission nodes (only the band's
+      //     perimeter can hold them): whole rows whose global row is a
+      //     transmission row (halo columns excluded: written by (b)), and the
+      //     columns of global column 0 / n0-1 when those are transmission
+      //     columns, in the other rows.
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int r = tid + q * NT;
+        if (r < SH) {
+          if (left) sv[r * SWp + 3] = hl[q];
+          if (right) sv[r * SWp + cols + 4] = hr[q];
+        }
+      }
+      if (corr != T(0)) {
+        const int cl = (dlx == 0 && i0 == 0) ? 4 : -1;
+        const int ch = (dhx >= 0 && right) ? cols + 3 : -1;
+        if (cl >= 0 || ch >= 0) {
+          for (int r = tid; r < SH; r += NT) {
+            const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
+            if (jj != dly && jj != dhy) {
+              if (cl >= 0) sv[r * SWp + cl] += corr;
+              if (ch >= 0) sv[r * SWp + ch] += corr;
+            }
+          }
+        }
+        const int cand[4] = {0, 1, SH - 2, SH - 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = cand[q];
+          bool dup = r < 0 || r >= SH;
+          for (int p2 = 0; p2 < q; ++p2) dup = dup || (cand[p2] == r);
+          if (dup) continue;
+          const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
+          if (jj == dly || jj == dhy)
+            for (int c = tid; c < SWp; c += NT)
+              if (!(left && c == 3) && !(right && c == cols + 4)) sv[r * SWp + c] += corr;
         }
       }
       __syncthreads();  // S2: band staged
@@ -779,14 +784,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
       rec.nonfinite = cnt;
       rec.sub = H.w.sub;
       a.part[t] = rec;
-      __threadfence();
-      const unsigned int prev = atomicAdd(&a.st[H.w.prob].tiles_done, 1u);
-      s_last = (prev == (unsigned int)(H.ph.ntiles - 1));
-    }
-    __syncthreads();  // S4
-    if (s_last) {
-      __threadfence();
-      finish_problem<NT>(a, H.w.prob, phase);
     }
   }
   if (tid == 0) queue_exit(a);
@@ -803,7 +800,6 @@ __global__ void __launch_bounds__(TX * TY) k_sweep3d(LaunchArgs a) {
   __shared__ T red_t[4 * (NT / 32)];
   __shared__ T red_f[3 * (NT / 32)];
   __shared__ int red_i[NT / 32];
-  __shared__ int s_last;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   const int tend = a.t0 + a.nwork;
@@ -909,7 +905,6 @@ __global__ void __launch_bounds__(TX * TY) k_sweep3d(LaunchArgs a) {
       }
     }
     tile_reduce<T, NT>(th, l2a, l2b, ws, acc, a.part + t, S.w.sub, red_t, red_f, red_i);
-    arrive<NT>(a, S.w.prob, S.ph.ntiles, phase, &s_last);
   }
   if (tid == 0) queue_exit(a);
 }
