@@ -303,6 +303,40 @@ pma_status pma_solve(int device, const pma_grid *grid, const pma_monitor *monito
                      const pma_decomp *decomp, const pma_params *params, const double *psi0,
                      double *x_out, double *psi_out, pma_info *info);
 
+/* Allocation-free solve (the paper has no counterpart: this is a service
+ * for callers that must not allocate device memory).  Some programs cannot
+ * call cudaMalloc at this point: a host application that reserved the whole
+ * device for its own memory pool up front, a framework whose caching
+ * allocator owns every byte it hands out, or latency-critical code that may
+ * not risk the device-wide synchronisation an allocation or a free can
+ * cause.  This call runs one request to completion on the current device
+ * using only a fixed scratch area that lives inside this library
+ * (PMA_STATIC_SCRATCH_BYTES per GPU, reserved when the library is loaded on
+ * a device and held until the process exits); it calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   grid, monitor, decomp, params  the request (host structs, as pma_submit)
+ *   psi0_dev   optional warm start, DEVICE memory, N doubles (NULL: Psi^0 =
+ *              |xi|^2/2)
+ *   x_dev      output, DEVICE memory, dim*N doubles, component-major
+ *   info       optional, host
+ *   cuda_stream  stream to run on (NULL: the legacy default stream); the
+ *              call returns after the stream has finished its work.
+ * Requests whose state, tables and records do not fit the scratch area are
+ * rejected with PMA_ERR_NOMEM (pma_last_error gives the bytes needed); the
+ * transmission must be PMA_TRANSMISSION_PARALLEL.  Every call shares the
+ * same scratch area: calls that overlap on the GPU (two streams, two host
+ * threads, or a call racing a previous call still in flight on another
+ * stream) corrupt each other.  The first call on a device also performs a
+ * one-time set-up (it looks up the scratch area's device address), so make
+ * the first call on each device before any stream capture begins.
+ * Returns the request's final status (PMA_OK, PMA_NOT_CONVERGED,
+ * PMA_ERR_TANGLED) or an error.                                             */
+#define PMA_STATIC_SCRATCH_BYTES (32u << 20)
+pma_status pma_solve_static(const pma_grid *grid, const pma_monitor *monitor,
+                            const pma_decomp *decomp, const pma_params *params,
+                            const double *psi0_dev, double *x_dev, pma_info *info,
+                            void *cuda_stream);
+
 /* ------------------------------------------------------------ misc */
 const char *pma_status_str(int32_t status);
 /* Last CUDA / validation error text of this thread (never NULL). */

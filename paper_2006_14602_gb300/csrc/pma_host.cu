@@ -1255,3 +1255,221 @@ pma_status pma_solve(int device, const pma_grid* grid, const pma_monitor* mon,
 }
 
 }  // extern "C"
+
+// ============================================================== no-allocation solve
+// pma_solve_static runs one request with every intermediate buffer (state,
+// tables, tile records, counters) carved out of one fixed scratch array
+// that belongs to this library's device code, for callers that must not
+// allocate device memory.  The array is reserved on each GPU the library is
+// loaded on and held until the process exits.
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[PMA_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxStaticDevices] = {};
+
+// Device address of the scratch array on device `dev` (current).  In host
+// code the array's name is only a stand-in, so the address is looked up
+// once per device and cached.
+pma_status static_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxStaticDevices) {
+    set_err("pma_solve_static: device index out of range");
+    return PMA_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      set_err(std::string("pma_solve_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      return PMA_ERR_CUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return PMA_OK;
+}
+
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off = (off + bytes + 255) & ~(size_t)255;
+    return o;
+  }
+};
+
+}  // namespace
+
+extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* mon,
+                                       const pma_decomp* dec, const pma_params* par,
+                                       const double* psi0_dev, double* x_dev, pma_info* info,
+                                       void* cuda_stream) {
+  if (!grid || !mon || !par || !x_dev) return PMA_ERR_INVALID;
+  Request r;
+  r.g = *grid;
+  r.m = *mon;
+  if (dec) {
+    r.d = *dec;
+  } else {
+    r.d.parts[0] = r.d.parts[1] = r.d.parts[2] = 1;
+    r.d.overlap = 0;
+    r.d.transmission = PMA_TRANSMISSION_PARALLEL;
+  }
+  r.p = *par;
+  pma_status st = build_request(r);  // state layout (no warm start block)
+  if (st != PMA_OK) return st;
+  int dev = 0;
+  PMA_CK(cudaGetDevice(&dev));
+  void* base = nullptr;
+  if ((st = static_scratch(dev, &base)) != PMA_OK) return st;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const auto t_start = Clock::now();
+
+  // work items of the request (default work shapes), slot 0
+  const int cls = r.cls;
+  const Tile2D t2 = tile2d_shape(0, r.esize == 8);
+  const Tile3D t3 = tile3d_shape(0);
+  r.slot = 0;
+  std::vector<SubDesc> subs;
+  std::vector<WorkItem> work;
+  for (size_t si = 0; si < r.subs.size(); ++si) {
+    const HostSub& hs = r.subs[si];
+    SubDesc sd{};
+    sd.prob = 0;
+    for (int a = 0; a < 3; ++a) {
+      sd.n[a] = hs.n[a];
+      sd.g0[a] = hs.g0[a];
+      sd.clo[a] = hs.clo[a];
+      sd.chi[a] = hs.chi[a];
+      sd.k[a] = hs.k[a];
+    }
+    sd.faces = hs.faces;
+    sd.idx = hs.idx;
+    sd.pitch = hs.pitch;
+    sd.tile_begin = (int)work.size();
+    const int sidx = (int)si;
+    if (r.dim == 2) {
+      for (int x = 0; x < hs.n[0]; x += t2.cols) {
+        const int cols = std::min(t2.cols, hs.n[0] - x);
+        const int swp = ((cols + 3) & ~3) + 8;
+        int rows = std::max(1, std::min(hs.n[1], t2.nodes / ((cols + 3) & ~3)));
+        while (rows > 1 && ((rows + 2) * swp > t2.smax || rows + 2 > 2 * t2.threads)) --rows;
+        for (int y = 0; y < hs.n[1]; y += rows) {
+          const int rr = std::min(rows, hs.n[1] - y);
+          work.push_back(WorkItem{sidx, 0, x | (y << 16), cols | (rr << 16)});
+        }
+      }
+    } else {
+      for (int z = 0; z < hs.n[2]; z += t3.tz)
+        for (int y = 0; y < hs.n[1]; y += t3.ty)
+          for (int x = 0; x < hs.n[0]; x += t3.tx) {
+            const int d = std::min(t3.tz, hs.n[2] - z);
+            work.push_back(WorkItem{sidx, 0, x | (y << 16), z | (d << 16)});
+          }
+    }
+    sd.tile_end = (int)work.size();
+    subs.push_back(sd);
+  }
+
+  // scratch layout; everything must fit the fixed array
+  Carve cv;
+  const size_t o_subs = cv.take(sizeof(SubDesc) * subs.size());
+  const size_t o_work = cv.take(sizeof(WorkItem) * work.size());
+  const size_t o_part = cv.take(sizeof(Partial) * work.size());
+  const size_t o_prob = cv.take(sizeof(ProbDesc));
+  const size_t o_hotf = cv.take(sizeof(ProbHot<float>));
+  const size_t o_hotd = cv.take(sizeof(ProbHot<double>));
+  const size_t o_st = cv.take(sizeof(ProbState));
+  const size_t o_q = cv.take(sizeof(unsigned int) * 2 * NUM_CLS);
+  const size_t o_fin = cv.take(sizeof(int));
+  const size_t o_job = cv.take(sizeof(CombineJob));
+  const size_t o_v = cv.take(r.bytes);
+  if (cv.off > (size_t)PMA_STATIC_SCRATCH_BYTES) {
+    set_err("pma_solve_static: request needs " + std::to_string(cv.off) +
+            " bytes of scratch, the fixed area holds " +
+            std::to_string((size_t)PMA_STATIC_SCRATCH_BYTES));
+    return PMA_ERR_NOMEM;
+  }
+  char* B = (char*)base;
+  r.block = B + o_v;
+  for (SubDesc& sd : subs) {
+    const HostSub& hs = r.subs[sd.idx];
+    sd.v[0] = r.block + hs.off[0];
+    sd.v[1] = r.block + hs.off[1];
+  }
+  ProbDesc pd;
+  fill_probdesc(r, pd);
+  pd.sub_base = 0;
+  pd.tile_begin = 0;
+  pd.tile_end = (int)work.size();
+  pd.psi0 = psi0_dev;
+  ProbHot<float> hf;
+  ProbHot<double> hd;
+  fill_hot<float>(r, pd, hf);
+  fill_hot<double>(r, pd, hd);
+  ProbState ps{};
+  ps.phase = PH_INIT_V;
+  ps.status = PMA_PENDING;
+  const int fin = 0;
+
+  // upload (clears the counters and the problem scalars of any earlier call)
+  PMA_CK(cudaMemcpyAsync(B + o_subs, subs.data(), sizeof(SubDesc) * subs.size(),
+                         cudaMemcpyHostToDevice, s));
+  PMA_CK(cudaMemcpyAsync(B + o_work, work.data(), sizeof(WorkItem) * work.size(),
+                         cudaMemcpyHostToDevice, s));
+  PMA_CK(cudaMemcpyAsync(B + o_prob, &pd, sizeof(pd), cudaMemcpyHostToDevice, s));
+  PMA_CK(cudaMemcpyAsync(B + o_hotf, &hf, sizeof(hf), cudaMemcpyHostToDevice, s));
+  PMA_CK(cudaMemcpyAsync(B + o_hotd, &hd, sizeof(hd), cudaMemcpyHostToDevice, s));
+  PMA_CK(cudaMemcpyAsync(B + o_st, &ps, sizeof(ps), cudaMemcpyHostToDevice, s));
+  PMA_CK(cudaMemcpyAsync(B + o_fin, &fin, sizeof(fin), cudaMemcpyHostToDevice, s));
+  PMA_CK(cudaMemsetAsync(B + o_q, 0, sizeof(unsigned int) * 2 * NUM_CLS, s));
+  PMA_CK(cudaStreamSynchronize(s));
+
+  int num_sms = 1;
+  PMA_CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  LaunchArgs la;
+  la.hotf = (const ProbHot<float>*)(B + o_hotf);
+  la.hotd = (const ProbHot<double>*)(B + o_hotd);
+  la.work = (const WorkItem*)(B + o_work);
+  la.t0 = 0;
+  la.nwork = (int)work.size();
+  la.subs = (const SubDesc*)(B + o_subs);
+  la.probs = (const ProbDesc*)(B + o_prob);
+  la.st = (ProbState*)(B + o_st);
+  la.part = (Partial*)(B + o_part);
+  la.queue = (unsigned int*)(B + o_q) + 2 * cls;
+  la.grid = std::min(la.nwork, sweep_max_blocks_per_sm(cls, 0) * num_sms);
+
+  // step in windows until the request is done (two extra launches cover
+  // the initial-state and theta^0 passes)
+  const int window = 64;
+  for (;;) {
+    for (int k = 0; k < window; ++k) {
+      PMA_CK(launch_sweep(cls, 0, la, s));
+      PMA_CK(launch_finish((const int*)(B + o_fin), 1, la.subs, la.probs, la.st, la.part, s));
+    }
+    PMA_CK(cudaMemcpyAsync(&ps, B + o_st, sizeof(ps), cudaMemcpyDeviceToHost, s));
+    PMA_CK(cudaStreamSynchronize(s));
+    if (ps.phase == PH_DONE) break;
+  }
+
+  // owner-takes combination into the caller's buffer
+  const CombineJob job{0, 1, x_dev, nullptr};
+  PMA_CK(cudaMemcpyAsync(B + o_job, &job, sizeof(job), cudaMemcpyHostToDevice, s));
+  PMA_CK(launch_combine((const CombineJob*)(B + o_job), 1, r.nodes, la.subs, la.probs, la.st, s));
+  PMA_CK(cudaStreamSynchronize(s));
+  if (info) {
+    info->steps = ps.step;
+    info->residual = ps.residual;
+    info->theta = ps.theta;
+    info->min_det = ps.min_det;
+    info->shift = ps.shift;
+    info->status = ps.status;
+    info->reserved = 0;
+    info->latency_us = std::chrono::duration<double, std::micro>(Clock::now() - t_start).count();
+  }
+  return (pma_status)ps.status;
+}

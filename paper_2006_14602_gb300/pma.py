@@ -134,6 +134,9 @@ _SIGS = {
     "pma_solve": (C.c_int, [C.c_int, _P(pma_grid), _P(pma_monitor), _P(pma_decomp),
                             _P(pma_params), _P(C.c_double), _P(C.c_double), _P(C.c_double),
                             _P(pma_info)]),
+    "pma_solve_static": (C.c_int, [_P(pma_grid), _P(pma_monitor), _P(pma_decomp),
+                                   _P(pma_params), C.c_void_p, C.c_void_p, _P(pma_info),
+                                   C.c_void_p]),
 }
 
 
@@ -434,3 +437,17 @@ def solve_many(probs: Sequence, device: int = 0, want_psi: bool = False, **optio
         ids = [ctx.submit(p) for p in probs]
         ctx.run()
         return [ctx.mesh(p, i, want_psi) for p, i in zip(probs, ids)]
+
+
+PMA_STATIC_SCRATCH_BYTES = 32 << 20
+
+
+def pma_solve_static(grid, monitor, decomp, params, psi0_dev_ptr: int, x_dev_ptr: int,
+                     cuda_stream: int = 0):
+    """Allocation-free solve: device pointers in and out, fixed library scratch."""
+    info = pma_info()
+    st = _call("pma_solve_static", C.byref(grid), C.byref(monitor),
+               C.byref(decomp) if decomp is not None else None, C.byref(params),
+               C.c_void_p(psi0_dev_ptr or None), C.c_void_p(x_dev_ptr), C.byref(info),
+               C.c_void_p(cuda_stream or None))
+    return st, info
