@@ -152,7 +152,7 @@ def _sub_nodes(prob) -> int:
     return total
 
 
-def oracle_sample(probs, budget_node_updates: float = 3.0e8, seed: int = 7):
+def oracle_sample(probs, budget_node_updates: float = 1.2e9, seed: int = 7):
     """A bounded sample of the workload for the CPU oracle: a seeded subset
     of requests with their step caps scaled so that the whole sample is about
     budget_node_updates of work."""
@@ -199,10 +199,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(workload: str, precision: str):
+def recorded_traffic(kernel: str, workload: str, precision: str):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
     taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "sweep_%s_%s.md" % (workload, precision))
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
     if not os.path.exists(path):
         return None, None
     src = None
@@ -416,7 +416,8 @@ def main():
     a0 = agg[0]
     peak, peak_kind = measured_peaks()
     achieved = a0["sweep_bytes"] / (a0["sweep_ms"] / 1e3) / 1e9
-    traffic, tpath = recorded_traffic(args.workload, args.precision)
+    kname = "k_band2d" if probs[0].dim == 2 else "k_sweep3d"
+    traffic, tpath = recorded_traffic(kname, args.workload, args.precision)
     lat = [x for x in a0["lat"] if x is not None]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -438,7 +439,7 @@ def main():
         "gpu_launches": a0["launches"] // max(args.steps, 1),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,
-                     "kernel": "k_sweep2d" if probs[0].dim == 2 else "k_sweep3d",
+                     "kernel": kname,
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
                      "algorithmic_bytes_per_node_update": 2 * (4 if args.precision == "fp32" else 8)},
         "cpu_baseline": cpu,
