@@ -351,7 +351,10 @@ def _info(pma, ctx, rid):
 def _barrier(world, device):
     if world > 1:
         import torch.distributed as dist
-        dist.barrier(device_ids=[device])
+        if dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
 
 
 def _gather(world, local, device):
@@ -361,6 +364,15 @@ def _gather(world, local, device):
     out = [None] * world
     dist.all_gather_object(out, local)
     return out
+
+
+def aggregate(agg):
+    """Whole-job throughput over replicas: every rank's node-updates over the
+    slowest rank's time (device-resident and end to end)."""
+    nu = sum(a["node_updates"] for a in agg)
+    ms = max(a["ms"] for a in agg)
+    e2e = sum(a["e2e_nu"] for a in agg) / (max(a["e2e_ms"] for a in agg) / 1e3)
+    return nu / (ms / 1e3), ms, e2e
 
 
 # ------------------------------------------------------------------ main
@@ -409,10 +421,7 @@ def main():
     agg, clocks, probs = native(args, rank, world, local_rank)
     if rank != 0:
         return 0
-    nu = sum(a["node_updates"] for a in agg)
-    ms = max(a["ms"] for a in agg)
-    value = nu / (ms / 1e3)
-    e2e_v = sum(a["e2e_nu"] for a in agg) / (max(a["e2e_ms"] for a in agg) / 1e3)
+    value, ms, e2e_v = aggregate(agg)
     a0 = agg[0]
     peak, peak_kind = measured_peaks()
     achieved = a0["sweep_bytes"] / (a0["sweep_ms"] / 1e3) / 1e9

@@ -473,7 +473,9 @@ pma_status rebuild(pma_ctx* c) {
             const int cols = std::min(t2.cols, hs.n[0] - x);
             const int swp = ((cols + 3) & ~3) + 8;
             int rows = std::max(1, std::min(hs.n[1], t2.nodes / ((cols + 3) & ~3)));
-            while (rows > 1 && ((rows + 2) * swp > t2.smax || rows + 2 > 2 * t2.threads)) --rows;
+            const int cr = (cols + 3) & ~3;
+            while (rows > 1 && ((rows + 2) * swp + 3 * cr > t2.smax || rows + 2 > 2 * t2.threads))
+              --rows;
             for (int y = 0; y < hs.n[1]; y += rows) {
               const int rr = std::min(rows, hs.n[1] - y);
               wl.push_back(WorkItem{sidx, r.slot, x | (y << 16), cols | (rr << 16)});
@@ -1356,7 +1358,9 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
         const int cols = std::min(t2.cols, hs.n[0] - x);
         const int swp = ((cols + 3) & ~3) + 8;
         int rows = std::max(1, std::min(hs.n[1], t2.nodes / ((cols + 3) & ~3)));
-        while (rows > 1 && ((rows + 2) * swp > t2.smax || rows + 2 > 2 * t2.threads)) --rows;
+        const int cr = (cols + 3) & ~3;
+        while (rows > 1 && ((rows + 2) * swp + 3 * cr > t2.smax || rows + 2 > 2 * t2.threads))
+          --rows;
         for (int y = 0; y < hs.n[1]; y += rows) {
           const int rr = std::min(rows, hs.n[1] - y);
           work.push_back(WorkItem{sidx, 0, x | (y << 16), cols | (rr << 16)});

@@ -431,6 +431,47 @@ struct Vec4<double> {
   }
 };
 
+// Pairs of values of the sweep precision.  FP32 pairs map to the packed
+// FFMA2 / FADD2 / FMUL2 instructions of sm_100-family GPUs (two nodes per
+// instruction); FP64 pairs are two scalar operations.
+template <typename T>
+struct P2;
+template <>
+struct P2<float> {
+  float2 v;
+  __device__ __forceinline__ float x() const { return v.x; }
+  __device__ __forceinline__ float y() const { return v.y; }
+  __device__ __forceinline__ static P2 mk(float a, float b) { return P2{make_float2(a, b)}; }
+  __device__ __forceinline__ static P2 s(float a) { return P2{make_float2(a, a)}; }
+};
+template <>
+struct P2<double> {
+  double a, b;
+  __device__ __forceinline__ double x() const { return a; }
+  __device__ __forceinline__ double y() const { return b; }
+  __device__ __forceinline__ static P2 mk(double p, double q) { return P2{p, q}; }
+  __device__ __forceinline__ static P2 s(double p) { return P2{p, p}; }
+};
+__device__ __forceinline__ P2<float> padd(P2<float> a, P2<float> b) { return P2<float>{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ P2<float> pmul(P2<float> a, P2<float> b) { return P2<float>{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ P2<float> pfma(P2<float> a, P2<float> b, P2<float> c) {
+  return P2<float>{__ffma2_rn(a.v, b.v, c.v)};
+}
+// a - b with one rounding, as a scalar subtraction
+__device__ __forceinline__ P2<float> psub(P2<float> a, P2<float> b) {
+  return P2<float>{__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v)};
+}
+__device__ __forceinline__ P2<double> padd(P2<double> a, P2<double> b) { return {a.a + b.a, a.b + b.b}; }
+__device__ __forceinline__ P2<double> pmul(P2<double> a, P2<double> b) { return {a.a * b.a, a.b * b.b}; }
+__device__ __forceinline__ P2<double> pfma(P2<double> a, P2<double> b, P2<double> c) {
+  return {fma(a.a, b.a, c.a), fma(a.b, b.b, c.b)};
+}
+__device__ __forceinline__ P2<double> psub(P2<double> a, P2<double> b) { return {a.a - b.a, a.b - b.b}; }
+template <typename T>
+__device__ __forceinline__ P2<T> pexw(P2<T> a) {
+  return P2<T>::mk(Fm<T>::exw(a.x()), Fm<T>::exw(a.y()));
+}
+
 // 16-byte chunk copy global -> shared (VW elements of T).
 template <typename T>
 __device__ __forceinline__ void copy16(T* d, const T* s) {
@@ -639,6 +680,31 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
         if (q < nterms && H.ph.mon.t[q].type != PMA_TERM_BUMP && H.ph.mon.t[q].type != PMA_TERM_RING)
           fast = false;
 
+      // Per-column tables of the band (after the staged rows in shared
+      // memory): theta weight of owned columns (0 elsewhere), 1 for updated
+      // columns (inside the band, not a transmission column), and the local
+      // trapezoid weight for the L2 increment.
+      const int cr = (cols + 3) & ~3;
+      T* wcol = sv + SH * SWp;
+      T* ucol = wcol + cr;
+      T* lcol = ucol + cr;
+      for (int c = tid; c < cr; c += NT) {
+        const int i = i0 + c, gi = g00 + i;
+        const bool valid = c < cols;
+        wcol[c] = (valid && i >= clo0 && i <= chi0) ? ((gi == 0 || gi == N0 - 1) ? hw0 : h0) : T(0);
+        ucol[c] = (valid && i != dlx && i != dhx) ? T(1) : T(0);
+        lcol[c] = (i == 0 || i == n0 - 1) ? hw0 : h0;
+      }
+      __syncthreads();
+      // partial sums: theta, sum of (G - c) over updated nodes (a non-finite
+      // value anywhere makes it non-finite), extrema of G - c, min det
+      P2<T> th2 = P2<T>::s(T(0)), gs2 = P2<T>::s(T(0));
+      T gcmax = -big_val<T>(), gcmin = big_val<T>();
+      const P2<T> NCL = P2<T>::s(-c_lag), DT2 = P2<T>::s(dt), M1 = P2<T>::s(T(-1));
+      const P2<T> M2 = P2<T>::s(T(-2)), ONE = P2<T>::s(T(1));
+      const P2<T> I2H0 = P2<T>::s(inv2h0), I2H1 = P2<T>::s(inv2h1);
+      const P2<T> IH20 = P2<T>::s(invh20), IH21 = P2<T>::s(invh21);
+      const P2<T> INV4 = P2<T>::s(inv4), NINV4 = P2<T>::s(-inv4);
       for (int q = tid; q < nruns; q += NT) {
         const int r = qdiv(q, rpr, inv_rpr), c0 = (q - r * rpr) * 4;
         const int j = j0 + r, gj = g01 + j;
@@ -660,73 +726,110 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
           wN[1] = m.v[0]; wN[2] = m.v[1]; wN[3] = m.v[2]; wN[4] = m.v[3];
           wN[5] = p[SWp + 4];
         }
+        Vec4<T> wc, uc;
+        wc.lds(wcol + c0);
+        uc.lds(ucol + c0);
         const bool rowdir = (j == dly || j == dhy);
-        const bool rowown = (j >= clo1 && j <= chi1);
-        const T wy = (gj == 0 || gj == N1 - 1) ? hw1 : h1;
-        const T wly = (j == 0 || j == n1 - 1) ? hw1 : h1;
+        const T wyo = (j >= clo1 && j <= chi1) ? ((gj == 0 || gj == N1 - 1) ? hw1 : h1) : T(0);
         const T xi1 = fma((T)gj, h1, lo1);
-        T x0[4], x1[4], D[4], rho[4];
+        const int gi0 = g00 + i0 + c0;
+        const P2<T> dA = psub(P2<T>::mk(wN[0], wN[1]), P2<T>::mk(wS[0], wS[1]));
+        const P2<T> dB = psub(P2<T>::mk(wN[2], wN[3]), P2<T>::mk(wS[2], wS[3]));
+        const P2<T> dC = psub(P2<T>::mk(wN[4], wN[5]), P2<T>::mk(wS[4], wS[5]));
+        P2<T> X0[2], X1[2], DD[2], R[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const T vc = wC[u + 1], ve = wC[u + 2], vw = wC[u];
-          const T vn = wN[u + 1], vs = wS[u + 1];
-          const int gi = g00 + i0 + c0 + u;
-          x0[u] = fma((T)gi, h0, lo0) + (ve - vw) * inv2h0;
-          x1[u] = xi1 + (vn - vs) * inv2h1;
-          const T hxx = fma(ve - T(2) * vc + vw, invh20, T(1));
-          const T hyy = fma(vn - T(2) * vc + vs, invh21, T(1));
-          const T hxy = ((wN[u + 2] - wS[u + 2]) - (wN[u] - wS[u])) * inv4;
-          D[u] = fma(hxx, hyy, -hxy * hxy);
+        for (int pp = 0; pp < 2; ++pp) {
+          const P2<T> C = P2<T>::mk(wC[2 * pp + 1], wC[2 * pp + 2]);
+          const P2<T> E = P2<T>::mk(wC[2 * pp + 2], wC[2 * pp + 3]);
+          const P2<T> Wv = P2<T>::mk(wC[2 * pp], wC[2 * pp + 1]);
+          const P2<T> Nn = P2<T>::mk(wN[2 * pp + 1], wN[2 * pp + 2]);
+          const P2<T> Ss = P2<T>::mk(wS[2 * pp + 1], wS[2 * pp + 2]);
+          const P2<T> XI0 = P2<T>::mk(fma((T)(gi0 + 2 * pp), h0, lo0),
+                                      fma((T)(gi0 + 2 * pp + 1), h0, lo0));
+          X0[pp] = pfma(psub(E, Wv), I2H0, XI0);
+          X1[pp] = pfma(psub(Nn, Ss), I2H1, P2<T>::s(xi1));
+          const P2<T> hxx = pfma(pfma(C, M2, padd(E, Wv)), IH20, ONE);
+          const P2<T> hyy = pfma(pfma(C, M2, padd(Nn, Ss)), IH21, ONE);
+          const P2<T> df = pp == 0 ? psub(dB, dA) : psub(dC, dB);
+          DD[pp] = pfma(pmul(df, INV4), pmul(df, NINV4), pmul(hxx, hyy));
         }
         if (fast) {
-          const T base = H.ph.mon.base;
+          // sum of Gaussian bumps / rings, two nodes per operation
 #pragma unroll
-          for (int u = 0; u < 4; ++u) rho[u] = base;
+          for (int pp = 0; pp < 2; ++pp) R[pp] = P2<T>::s(H.ph.mon.base);
           for (int k = 0; k < nterms; ++k) {
             const auto& tm = H.ph.mon.t[k];
-            const T cx = tm.c[0], cy = tm.c[1], r2 = tm.r2, nw = -tm.width, amp = tm.amp;
+            const P2<T> CX = P2<T>::s(tm.c[0]), CY = P2<T>::s(tm.c[1]), R2 = P2<T>::s(tm.r2);
+            const P2<T> NWd = P2<T>::s(-tm.width), AMP = P2<T>::s(tm.amp);
             const bool ring = tm.type == PMA_TERM_RING;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const T d0 = x0[u] - cx, d1 = x1[u] - cy;
-              const T qq = fma(d0, d0, d1 * d1);
-              const T s2 = qq - r2;
-              const T uu = ring ? s2 * s2 : qq;
-              rho[u] = fma(amp, Fm<T>::exw(nw * uu), rho[u]);
+            for (int pp = 0; pp < 2; ++pp) {
+              const P2<T> d0 = psub(X0[pp], CX), d1 = psub(X1[pp], CY);
+              const P2<T> qq = pfma(d0, d0, pmul(d1, d1));
+              const P2<T> s2 = psub(qq, R2);
+              const P2<T> uu = ring ? pmul(s2, s2) : qq;
+              R[pp] = pfma(AMP, pexw<T>(pmul(uu, NWd)), R[pp]);
             }
           }
         } else {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) rho[u] = rho_at<T>(H.ph.mon, x0[u], x1[u], T(0));
+          for (int pp = 0; pp < 2; ++pp)
+            R[pp] = P2<T>::mk(rho_at<T>(H.ph.mon, X0[pp].x(), X1[pp].x(), T(0)),
+                              rho_at<T>(H.ph.mon, X0[pp].y(), X1[pp].y(), T(0)));
         }
         Vec4<T> o;
+        T gcv[4], rdv[4];
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp) {
+          const P2<T> rD = pmul(R[pp], DD[pp]);
+          P2<T> GC;
+          if (logrhs) {
+            GC = P2<T>::mk(Fm<T>::ln(rD.x()), Fm<T>::ln(rD.y()));
+            GC = padd(GC, NCL);
+          } else {
+            GC = P2<T>::mk(Fm<T>::pw(scale_root * rD.x(), inv_dim) - T(1) - c_lag,
+                           Fm<T>::pw(scale_root * rD.y(), inv_dim) - T(1) - c_lag);
+          }
+          const P2<T> vn = pfma(GC, DT2, P2<T>::mk(wC[2 * pp + 1], wC[2 * pp + 2]));
+          o.v[2 * pp] = vn.x();
+          o.v[2 * pp + 1] = vn.y();
+          gcv[2 * pp] = GC.x();
+          gcv[2 * pp + 1] = GC.y();
+          rdv[2 * pp] = rD.x();
+          rdv[2 * pp + 1] = rD.y();
+        }
+        const T rowu = rowdir ? T(0) : T(1);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int c = c0 + u, i = i0 + c;
-          const bool valid = c < cols;
-          const bool dir = rowdir || i == dlx || i == dhx;
-          const T G = logrhs ? Fm<T>::ln(rho[u] * D[u])
-                             : Fm<T>::pw(scale_root * rho[u] * D[u], inv_dim) - T(1);
-          o.v[u] = fma(dt, G - c_lag, wC[u + 1]);
-          if (valid && !dir) {
-            if (!isfinite(G)) acc.nf += 1;
-            acc.gmax = fmax(acc.gmax, G);
-            acc.gmin = fmin(acc.gmin, G);
-            acc.dmin = fmin(acc.dmin, D[u]);
-            const int gi = g00 + i;
-            if (rowown && i >= clo0 && i <= chi0) {
-              const T wx = (gi == 0 || gi == N0 - 1) ? hw0 : h0;
-              th = fma(wx * wy, rho[u] * D[u], th);
-            }
-            if (want_l2) {
-              const T w = ((i == 0 || i == n0 - 1) ? hw0 : h0) * wly;
-              const T d = G - c_lag;
-              l2a = fma(w * d, d, l2a);
-              l2b = fma(w, d, l2b);
-              ws += w;
-            }
+          const bool upd = uc.v[u] * rowu != T(0);
+          const T dv = u < 2 ? (u == 0 ? DD[0].x() : DD[0].y()) : (u == 2 ? DD[1].x() : DD[1].y());
+          gcmax = fmax(gcmax, upd ? gcv[u] : -big_val<T>());
+          gcmin = fmin(gcmin, upd ? gcv[u] : big_val<T>());
+          acc.dmin = fmin(acc.dmin, upd ? dv : big_val<T>());
+          const T g = upd ? gcv[u] : T(0);
+          const T rd = upd ? rdv[u] : T(0);
+          if (u & 1) {
+            gs2 = padd(gs2, P2<T>::mk(T(0), g));
+            th2 = pfma(P2<T>::mk(T(0), wc.v[u] * wyo), P2<T>::mk(T(0), rd), th2);
+          } else {
+            gs2 = padd(gs2, P2<T>::mk(g, T(0)));
+            th2 = pfma(P2<T>::mk(wc.v[u] * wyo, T(0)), P2<T>::mk(rd, T(0)), th2);
           }
-          if (!valid) o.v[u] = T(0);
+          if (!upd) o.v[u] = T(0);
+        }
+        if (want_l2) {
+          Vec4<T> lc;
+          lc.lds(lcol + c0);
+          const T wly = (j == 0 || j == n1 - 1) ? hw1 : h1;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const bool upd = uc.v[u] * rowu != T(0);
+            const T w = upd ? lc.v[u] * wly : T(0);
+            const T d = upd ? gcv[u] : T(0);
+            l2a = fma(w * d, d, l2a);
+            l2b = fma(w, d, l2b);
+            ws += w;
+          }
         }
         if (run) {
           if (rowdir || (i0 + c0 <= dlx) || (i0 + c0 + 3 >= dhx && dhx >= 0)) {
@@ -740,6 +843,10 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
           o.stg(dst + j * pitch + i0 + c0);
         }
       }
+      th = th2.x() + th2.y();
+      if (gcmax > -big_val<T>()) acc.gmax = gcmax + c_lag;
+      if (gcmin < big_val<T>()) acc.gmin = gcmin + c_lag;
+      if (!isfinite(gs2.x() + gs2.y())) acc.nf += 1;
     }
     // tile record and arrival
     th = warp_sum(th);
@@ -933,8 +1040,10 @@ Tile2D tile2d_shape(int id, bool fp64) {
   t.threads = k_t2d[id][0];
   t.nodes = fp64 ? k_t2d[id][2] : k_t2d[id][1];
   t.smax = 3 * t.nodes;
-  // a one-row band plus halo must fit: 3 * (cols + 8) <= smax, cols % 4 == 0
-  t.cols = ((t.smax / 3 - 8) & ~3) < 1024 ? ((t.smax / 3 - 8) & ~3) : 1024;
+  // a one-row band plus halo and the three column tables must fit:
+  // 3 * (cols + 8) + 3 * cols <= smax, cols % 4 == 0
+  const int cmax = ((t.smax - 24) / 6) & ~3;
+  t.cols = cmax < 1024 ? cmax : 1024;
   return t;
 }
 Tile3D tile3d_shape(int id) { return k_t3d[id]; }
