@@ -426,6 +426,48 @@ int pick_tile(pma_ctx* c, int cls) {
   return (id >= 0 && id < tile3d_count()) ? id : 0;
 }
 
+// Work items of one subdomain (entry sidx of the subdomain table).
+//   2D: bands of full-width rows (strips of at most t2.cols columns), sized
+//       so that the staged band, its halo and the column tables fit;
+//   3D: boxes of cols x rows nodes per plane over tz planes.
+void push_items(const HostSub& hs, int dim, bool fp64, int tile_id, int sidx, int slot,
+                std::vector<WorkItem>& wl) {
+  if (dim == 2) {
+    const Tile2D t2 = tile2d_shape(tile_id, fp64);
+    for (int x = 0; x < hs.n[0]; x += t2.cols) {
+      const int cols = std::min(t2.cols, hs.n[0] - x);
+      const int cr = (cols + 3) & ~3;
+      const int swp = cr + 8;
+      int rows = std::max(1, std::min(hs.n[1], t2.nodes / cr));
+      while (rows > 1 && ((rows + 2) * swp + 3 * cr > t2.smax || rows + 2 > 2 * t2.threads))
+        --rows;
+      for (int y = 0; y < hs.n[1]; y += rows) {
+        const int rr = std::min(rows, hs.n[1] - y);
+        wl.push_back(WorkItem{sidx, slot, x | (y << 16), cols | (rr << 16), 0, {0, 0, 0}});
+      }
+    }
+  } else {
+    const Tile3D t3 = tile3d_shape(tile_id, fp64);
+    for (int x = 0; x < hs.n[0]; x += t3.cols) {
+      const int cols = std::min(t3.cols, hs.n[0] - x);
+      const int cr = (cols + 3) & ~3;
+      const int swp = cr + 8;
+      int rows = std::max(1, std::min(hs.n[1], t3.xy / cr));
+      while (rows > 1 && ((rows + 2) * swp * (t3.tz + 2) + 3 * cr > t3.smax ||
+                          (rows + 2) * (t3.tz + 2) > 8 * t3.threads))
+        --rows;
+      for (int y = 0; y < hs.n[1]; y += rows) {
+        const int rr = std::min(rows, hs.n[1] - y);
+        for (int z = 0; z < hs.n[2]; z += t3.tz) {
+          const int d = std::min(t3.tz, hs.n[2] - z);
+          wl.push_back(WorkItem{sidx, slot, x | (y << 16), cols | (rr << 16), z | (d << 16),
+                                {0, 0, 0}});
+        }
+      }
+    }
+  }
+}
+
 // Rebuild subdomain table, work lists and problem descriptors for the
 // current active + finished requests.  Only active requests get tiles.
 pma_status rebuild(pma_ctx* c) {
@@ -446,8 +488,6 @@ pma_status rebuild(pma_ctx* c) {
     std::vector<WorkItem>& wl = c->h_work[r.cls];
     const bool live = (r.state == RQ_ACTIVE);
     pd.tile_begin = (int)wl.size();
-    const Tile2D t2 = tile2d_shape(c->tile_id[r.cls], r.esize == 8);
-    const Tile3D t3 = tile3d_shape(c->tile_id[r.cls]);
     for (size_t si = 0; si < r.subs.size(); ++si) {
       const HostSub& hs = r.subs[si];
       SubDesc sd{};
@@ -465,31 +505,8 @@ pma_status rebuild(pma_ctx* c) {
       sd.v[0] = r.block + hs.off[0];
       sd.v[1] = r.block + hs.off[1];
       sd.tile_begin = (int)wl.size();
-      if (live) {
-        const int sidx = (int)c->h_subs.size();
-        if (r.dim == 2) {
-          // full-width row bands (strips of at most t2.cols columns)
-          for (int x = 0; x < hs.n[0]; x += t2.cols) {
-            const int cols = std::min(t2.cols, hs.n[0] - x);
-            const int swp = ((cols + 3) & ~3) + 8;
-            int rows = std::max(1, std::min(hs.n[1], t2.nodes / ((cols + 3) & ~3)));
-            const int cr = (cols + 3) & ~3;
-            while (rows > 1 && ((rows + 2) * swp + 3 * cr > t2.smax || rows + 2 > 2 * t2.threads))
-              --rows;
-            for (int y = 0; y < hs.n[1]; y += rows) {
-              const int rr = std::min(rows, hs.n[1] - y);
-              wl.push_back(WorkItem{sidx, r.slot, x | (y << 16), cols | (rr << 16)});
-            }
-          }
-        } else {
-          for (int z = 0; z < hs.n[2]; z += t3.tz)
-            for (int y = 0; y < hs.n[1]; y += t3.ty)
-              for (int x = 0; x < hs.n[0]; x += t3.tx) {
-                const int d = std::min(t3.tz, hs.n[2] - z);
-                wl.push_back(WorkItem{sidx, r.slot, x | (y << 16), z | (d << 16)});
-              }
-        }
-      }
+      if (live)
+        push_items(hs, r.dim, r.esize == 8, c->tile_id[r.cls], (int)c->h_subs.size(), r.slot, wl);
       sd.tile_end = (int)wl.size();
       c->h_subs.push_back(sd);
     }
@@ -827,6 +844,7 @@ pma_status pma_create(pma_ctx** out, int device, size_t mem_budget_bytes, void* 
     c->own_stream = true;
   }
   c->budget = mem_budget_bytes;
+  PMA_CK(prepare_sweep_kernels());
   pma_status st = ensure_slots(c.get(), 64);
   if (st != PMA_OK) return st;
   PMA_CK(cudaMalloc(&c->d_check, sizeof(double) * 4 + sizeof(unsigned long long)));
@@ -1332,8 +1350,6 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
 
   // work items of the request (default work shapes), slot 0
   const int cls = r.cls;
-  const Tile2D t2 = tile2d_shape(0, r.esize == 8);
-  const Tile3D t3 = tile3d_shape(0);
   r.slot = 0;
   std::vector<SubDesc> subs;
   std::vector<WorkItem> work;
@@ -1352,28 +1368,7 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
     sd.idx = hs.idx;
     sd.pitch = hs.pitch;
     sd.tile_begin = (int)work.size();
-    const int sidx = (int)si;
-    if (r.dim == 2) {
-      for (int x = 0; x < hs.n[0]; x += t2.cols) {
-        const int cols = std::min(t2.cols, hs.n[0] - x);
-        const int swp = ((cols + 3) & ~3) + 8;
-        int rows = std::max(1, std::min(hs.n[1], t2.nodes / ((cols + 3) & ~3)));
-        const int cr = (cols + 3) & ~3;
-        while (rows > 1 && ((rows + 2) * swp + 3 * cr > t2.smax || rows + 2 > 2 * t2.threads))
-          --rows;
-        for (int y = 0; y < hs.n[1]; y += rows) {
-          const int rr = std::min(rows, hs.n[1] - y);
-          work.push_back(WorkItem{sidx, 0, x | (y << 16), cols | (rr << 16)});
-        }
-      }
-    } else {
-      for (int z = 0; z < hs.n[2]; z += t3.tz)
-        for (int y = 0; y < hs.n[1]; y += t3.ty)
-          for (int x = 0; x < hs.n[0]; x += t3.tx) {
-            const int d = std::min(t3.tz, hs.n[2] - z);
-            work.push_back(WorkItem{sidx, 0, x | (y << 16), z | (d << 16)});
-          }
-    }
+    push_items(hs, r.dim, r.esize == 8, 0, (int)si, 0, work);
     sd.tile_end = (int)work.size();
     subs.push_back(sd);
   }
@@ -1434,6 +1429,7 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
 
   int num_sms = 1;
   PMA_CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  PMA_CK(prepare_sweep_kernels());
   LaunchArgs la;
   la.hotf = (const ProbHot<float>*)(B + o_hotf);
   la.hotd = (const ProbHot<double>*)(B + o_hotd);

@@ -122,7 +122,9 @@ struct alignas(16) WorkItem {
   int sub;
   int prob;
   int ij;    // i0 | j0 << 16
-  int ext;   // 2D: cols | rows << 16; 3D: k0 | depth << 16 (tile shape fixed)
+  int ext;   // cols | rows << 16
+  int kz;    // 3D: k0 | depth << 16 (planes); 2D: 0
+  int pad[3];
 };
 
 struct Partial {
@@ -136,13 +138,14 @@ struct Partial {
 };
 
 static_assert(sizeof(Partial) == 64, "partial record is one 64-byte line");
-static_assert(sizeof(WorkItem) == 16, "work item is 16 bytes");
+static_assert(sizeof(WorkItem) == 32, "work item is 32 bytes");
 
 // Work shapes.  2D: a band holds at most `nodes` nodes, at most `cols`
 // wide, processed by `threads` threads (shared staging of the band plus a
 // one-node halo); 3D: TX x TY threads marching TZ planes.
 struct Tile2D { int threads, nodes, smax, cols; };
-struct Tile3D { int tx, ty, tz; };
+// 3D: a box of at most `xy` nodes per plane (cols x rows) over `tz` planes.
+struct Tile3D { int threads, xy, tz, smax, cols; };
 
 // Kernel launch entry points (pma_kernels.cu).
 struct LaunchArgs {
@@ -162,11 +165,14 @@ struct LaunchArgs {
 int tile2d_count();
 int tile3d_count();
 Tile2D tile2d_shape(int id, bool fp64);
-Tile3D tile3d_shape(int id);
+Tile3D tile3d_shape(int id, bool fp64);
 
 // cls selects dim/precision; tile_id a compiled tile shape.
 cudaError_t launch_sweep(int cls, int tile_id, const LaunchArgs& a, cudaStream_t s);
 int sweep_max_blocks_per_sm(int cls, int tile_id);
+// Opt every sweep kernel into its dynamic shared-memory size (current
+// device); called when a context is created.
+cudaError_t prepare_sweep_kernels();
 
 // After a sweep launch: fold the tile records of the listed problem slots
 // (one warp each) and advance their scalars.

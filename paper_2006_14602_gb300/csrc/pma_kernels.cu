@@ -897,121 +897,422 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
 }
 
 // ---------------------------------------------------------------- 3D sweep
-// TX x TY threads, each marching up to TZ planes of the tile.
-template <typename T, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY) k_sweep3d(LaunchArgs a) {
-  constexpr int NT = TX * TY;
-  constexpr int SX = TX + 2, SY = TY + 2, SZ = TZ + 2;
-  __shared__ __align__(16) T sv[SZ * SY * SX];
-  __shared__ SmemHdr<T> S;
-  __shared__ T red_t[4 * (NT / 32)];
-  __shared__ T red_f[3 * (NT / 32)];
-  __shared__ int red_i[NT / 32];
-  const int tid = threadIdx.x;
-  const int tx = tid % TX, ty = tid / TX;
+// One work item is a box of cols x rows nodes per plane over `depth` planes
+// of one subdomain.  Staging mirrors the 2D band kernel (16-byte cp.async
+// copies of every staged row, mirror / clamp halos, the transmission offset
+// on the box perimeter).  Each thread takes runs of 4 consecutive x-nodes of
+// one row and marches them through the planes; per plane it reads the 46
+// values of the 19-point stencils of its 4 nodes with aligned vector loads.
+template <typename T, int NT, int TZ>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3d(LaunchArgs a) {
+  constexpr int VW = 16 / (int)sizeof(T);
+  constexpr int NW = NT / 32;
+  constexpr int HMAX = 8;  // halo rows per thread (host: (rows+2)(TZ+2) <= 8 NT)
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* sv = (T*)dyn_smem;     // staged box + column tables (dynamic size)
+  __shared__ __align__(16) SmemHdr<T> HB[2];
+  __shared__ int s_t[2];
+  __shared__ T red_t[4 * NW];
+  __shared__ T red_f[3 * NW];
+  __shared__ int red_i[NW];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int tend = a.t0 + a.nwork;
-  __shared__ int s_t;
-  int nt = 0;
-  WorkItem next;
+  int t_next = 0;
+  WorkItem w_next;
   if (tid == 0) {
-    nt = pull_item(a);
-    if (nt < tend) next = a.work[nt];
+    const int t0 = pull_item(a);
+    s_t[0] = t0;
+    if (t0 < tend) issue_hdr<T>(a, HB[0], a.work[t0]);
+    t_next = pull_item(a);
+    if (t_next < tend) w_next = a.work[t_next];
   }
 
-  for (;;) {
+  for (int it = 0;; ++it) {
+    const int b = it & 1;
+    if (tid == 0) cp_async_wait_all();
+    __syncthreads();  // header `b` complete and visible
+    const int t = s_t[b];
+    if (t >= tend) break;
     if (tid == 0) {
-      s_t = nt;
-      S.w = next;
-      if (nt < tend) {
-        nt = pull_item(a);
-        if (nt < tend) next = a.work[nt];
+      s_t[b ^ 1] = t_next;
+      if (t_next < tend) {
+        issue_hdr<T>(a, HB[b ^ 1], w_next);
+        t_next = pull_item(a);
+        if (t_next < tend) w_next = a.work[t_next];
       }
     }
-    __syncthreads();
-    const int t = s_t;
-    if (t >= tend) break;
-    load_hdr<T, NT>(a, S);
-    __syncthreads();
-    const int phase = S.ps.phase;
-    if (phase == PH_DONE) {
-      __syncthreads();
-      continue;
-    }
-    const int n0 = S.sd.n[0], n1 = S.sd.n[1], n2 = S.sd.n[2];
-    const int x0 = S.w.ij & 0xffff, y0 = S.w.ij >> 16;
-    const int z0 = S.w.ext & 0xffff, depth = S.w.ext >> 16;
-    const int faces = S.sd.faces;
-    const bool plx = faces & 1, phx = faces & 2, ply = faces & 4, phy = faces & 8;
-    const bool plz = faces & 16, phz = faces & 32;
-    const int g00 = S.sd.g0[0], g01 = S.sd.g0[1], g02 = S.sd.g0[2];
-    const T* src = (const T*)S.sd.v[S.ps.parity];
-    T* dst = (T*)S.sd.v[S.ps.parity ^ 1];
+    SmemHdr<T>& H = HB[b];
+    const int phase = H.ps.phase;
+    if (phase == PH_DONE) continue;
+    const int n0 = H.sd.n[0], n1 = H.sd.n[1], n2 = H.sd.n[2];
+    const long long pitch = H.sd.pitch, ppitch = pitch * n1;
+    const int i0 = H.w.ij & 0xffff, j0 = H.w.ij >> 16;
+    const int cols = H.w.ext & 0xffff, rows = H.w.ext >> 16;
+    const int k0 = H.w.kz & 0xffff, depth = H.w.kz >> 16;
+    const int faces = H.sd.faces;
+    const int g00 = H.sd.g0[0], g01 = H.sd.g0[1], g02 = H.sd.g0[2];
+    const T* src = (const T*)H.sd.v[H.ps.parity];
+    T* dst = (T*)H.sd.v[H.ps.parity ^ 1];
+    const int cr = (cols + 3) & ~3;
+    const int rpr = cr >> 2;
+    const int nruns = rows * rpr;
+    const float inv_rpr = 1.0f / (float)rpr;
+    const int dlx = (faces & 1) ? -1 : 0, dhx = (faces & 2) ? -1 : n0 - 1;
+    const int dly = (faces & 4) ? -1 : 0, dhy = (faces & 8) ? -1 : n1 - 1;
+    const int dlz = (faces & 16) ? -1 : 0, dhz = (faces & 32) ? -1 : n2 - 1;
     T th = 0, l2a = 0, l2b = 0, ws = 0;
     Acc<T> acc{-big_val<T>(), big_val<T>(), big_val<T>(), 0};
-    const long long rowp = S.sd.pitch;
-    const long long pitch_z = rowp * n1;
-    const int i = x0 + tx, j = y0 + ty;
 
     if (phase == PH_INIT_V) {
-      const double* psi0 = a.probs[S.w.prob].psi0;
-      for (int r = 0; r < depth; ++r) {
-        const int l = z0 + r;
-        if (i < n0 && j < n1 && l < n2) {
-          const T v0 = init_value<T>(S, psi0, g00 + i, g01 + j, g02 + l);
-          st_global(dst + l * pitch_z + j * rowp + i, v0);
-          st_global((T*)src + l * pitch_z + j * rowp + i, v0);
+      const double* psi0 = a.probs[H.w.prob].psi0;
+      const int Nx = H.ph.N[0], Ny = H.ph.N[1];
+      for (int q = tid; q < nruns * depth; q += NT) {
+        const int l = q / nruns, q2 = q - l * nruns;
+        const int r = qdiv(q2, rpr, inv_rpr), c0 = (q2 - r * rpr) * 4;
+        const int j = j0 + r, kk = k0 + l;
+        Vec4<T> o;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + c0 + u;
+          T v0 = T(0);
+          if (psi0 && i < n0) {
+            const int gi = g00 + i, gj = g01 + j, gk = g02 + kk;
+            const double xi = (double)H.ph.lo[0] + (double)gi * H.ph.hd[0];
+            const double et = (double)H.ph.lo[1] + (double)gj * H.ph.hd[1];
+            const double ze = (double)H.ph.lo[2] + (double)gk * H.ph.hd[2];
+            v0 = (T)(psi0[((long long)gk * Ny + gj) * Nx + gi] - 0.5 * (xi * xi + et * et + ze * ze));
+          }
+          o.v[u] = v0;
         }
+        o.stg(dst + kk * ppitch + j * pitch + i0 + c0);
+        o.stg((T*)src + kk * ppitch + j * pitch + i0 + c0);
       }
     } else {
-      const T corr = (T)S.ps.corr;
-      const int SZa = depth + 2;
-      for (int idx = tid; idx < SX * SY * SZa; idx += NT) {
-        const int lz = idx / (SX * SY);
-        const int rem = idx - lz * SX * SY;
-        const int ly = rem / SX, lx = rem - ly * SX;
-        const int ii = reflect_clamp(x0 - 1 + lx, n0, plx, phx);
-        const int jj = reflect_clamp(y0 - 1 + ly, n1, ply, phy);
-        const int ll = reflect_clamp(z0 - 1 + lz, n2, plz, phz);
-        T val = __ldcg(src + ll * pitch_z + jj * rowp + ii);
-        if (is_dir(faces, 3, ii, jj, ll, n0, n1, n2)) val += corr;
-        sv[idx] = val;
-      }
-      __syncthreads();
-      const T c_lag = (T)S.ps.c_lag, dt = S.ph.dt;
-      const T scale_root = (T)(S.ph.vol / (T)S.ps.theta_prev);
-      for (int r = 0; r < depth; ++r) {
-        const int l = z0 + r;
-        if (i >= n0 || j >= n1 || l >= n2) continue;
-        const int gi = g00 + i, gj = g01 + j, gl = g02 + l;
-        const long long gidx = l * pitch_z + j * rowp + i;
-        if (is_dir(faces, 3, i, j, l, n0, n1, n2)) {
-          if (phase == PH_RUN) st_global(dst + gidx, gather_owner<T>(a, S, i, j, l));
-          continue;
+      const int SWp = cr + 8, SHY = rows + 2, SHZ = depth + 2;
+      const int PS = SHY * SWp;
+      const int cpr = SWp / VW;
+      const float inv_cpr = 1.0f / (float)cpr;
+      const int nrow = SHZ * SHY;
+      const float inv_shy = 1.0f / (float)SHY;
+      const bool plx = faces & 1, phx = faces & 2, ply = faces & 4, phy = faces & 8;
+      const bool plz = faces & 16, phz = faces & 32;
+      const T corr = (T)H.ps.corr;
+      // (a) 16-byte asynchronous copies of every staged row
+      for (int e = tid; e < nrow * cpr; e += NT) {
+        const int rr = qdiv(e, cpr, inv_cpr), k = e - rr * cpr;
+        const int gs = i0 - 4 + k * VW;
+        if (gs >= 0 && gs + VW <= pitch) {
+          const int lz = qdiv(rr, SHY, inv_shy), ly = rr - lz * SHY;
+          const int jj = reflect_clamp(j0 - 1 + ly, n1, ply, phy);
+          const int kk = reflect_clamp(k0 - 1 + lz, n2, plz, phz);
+          cp_async16(sv + lz * PS + ly * SWp + k * VW, src + kk * ppitch + jj * pitch + gs);
         }
-        const T* c = sv + ((r + 1) * SY + (ty + 1)) * SX + (tx + 1);
-        constexpr int PY = SX, PZ = SX * SY;
-        const T vc = c[0];
-        const T vxp = c[1], vxm = c[-1], vyp = c[PY], vym = c[-PY], vzp = c[PZ], vzm = c[-PZ];
-        const T xx = fma((T)gi, S.ph.h[0], S.ph.lo[0]) + (vxp - vxm) * S.ph.inv2h[0];
-        const T xy = fma((T)gj, S.ph.h[1], S.ph.lo[1]) + (vyp - vym) * S.ph.inv2h[1];
-        const T xz = fma((T)gl, S.ph.h[2], S.ph.lo[2]) + (vzp - vzm) * S.ph.inv2h[2];
-        const T hxx = T(1) + (vxp - T(2) * vc + vxm) * S.ph.invh2[0];
-        const T hyy = T(1) + (vyp - T(2) * vc + vym) * S.ph.invh2[1];
-        const T hzz = T(1) + (vzp - T(2) * vc + vzm) * S.ph.invh2[2];
-        const T hxy = ((c[PY + 1] - c[-PY + 1]) - (c[PY - 1] - c[-PY - 1])) * S.ph.inv4hh[0];
-        const T hxz = ((c[PZ + 1] - c[-PZ + 1]) - (c[PZ - 1] - c[-PZ - 1])) * S.ph.inv4hh[1];
-        const T hyz = ((c[PZ + PY] - c[-PZ + PY]) - (c[PZ - PY] - c[-PZ - PY])) * S.ph.inv4hh[2];
-        const T D = hxx * (hyy * hzz - hyz * hyz) - hxy * (hxy * hzz - hyz * hxz) +
-                    hxz * (hxy * hyz - hyy * hxz);
-        T rho;
-        const T G = rhs_value<T>(S, phase, scale_root, xx, xy, xz, D, rho);
-        const bool owned = i >= S.sd.clo[0] && i <= S.sd.chi[0] && j >= S.sd.clo[1] &&
-                           j <= S.sd.chi[1] && l >= S.sd.clo[2] && l <= S.sd.chi[2];
-        accumulate<T>(S, G, D, rho, owned, gi, gj, gl, i, j, l, c_lag, th, l2a, l2b, ws, acc);
-        if (phase == PH_RUN) st_global(dst + gidx, fma(dt, G - c_lag, vc));
       }
+      cp_async_commit();
+      // (b) x-halo columns (Neumann mirror; clamp on transmission faces)
+      const bool left = (i0 == 0), right = (i0 + cols == n0);
+      T hl[HMAX], hr[HMAX];
+#pragma unroll
+      for (int q = 0; q < HMAX; ++q) {
+        const int rr = tid + q * NT;
+        hl[q] = hr[q] = T(0);
+        if (rr < nrow && (left || right)) {
+          const int lz = qdiv(rr, SHY, inv_shy), ly = rr - lz * SHY;
+          const int jj = reflect_clamp(j0 - 1 + ly, n1, ply, phy);
+          const int kk = reflect_clamp(k0 - 1 + lz, n2, plz, phz);
+          const bool dr = (jj == dly || jj == dhy || kk == dlz || kk == dhz);
+          const T cc = dr ? corr : T(0);
+          const T* row = src + kk * ppitch + jj * pitch;
+          if (left && plx) hl[q] = __ldcg(row + 1) + cc;
+          if (right && phx) hr[q] = __ldcg(row + n0 - 2) + cc;
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      // (c) halos, then the transmission offset on the box perimeter:
+      //     transmission planes (whole), rows in other planes (whole),
+      //     columns 0 / n0-1 elsewhere; halo columns were written by (b)
+#pragma unroll
+      for (int q = 0; q < HMAX; ++q) {
+        const int rr = tid + q * NT;
+        if (rr < nrow) {
+          if (left) sv[rr * SWp + 3] = hl[q];
+          if (right) sv[rr * SWp + cols + 4] = hr[q];
+        }
+      }
+      if (corr != T(0)) {
+        const int cl = (dlx == 0 && i0 == 0) ? 4 : -1;
+        const int ch = (dhx >= 0 && right) ? cols + 3 : -1;
+        for (int rr = tid; rr < nrow; rr += NT) {
+          const int lz = qdiv(rr, SHY, inv_shy), ly = rr - lz * SHY;
+          const int jj = reflect_clamp(j0 - 1 + ly, n1, ply, phy);
+          const int kk = reflect_clamp(k0 - 1 + lz, n2, plz, phz);
+          T* row = sv + rr * SWp;
+          if (jj == dly || jj == dhy || kk == dlz || kk == dhz) {
+            for (int c = 0; c < SWp; ++c)
+              if (!(left && c == 3) && !(right && c == cols + 4)) row[c] += corr;
+          } else {
+            if (cl >= 0) row[cl] += corr;
+            if (ch >= 0) row[ch] += corr;
+          }
+        }
+      }
+      const T c_lag = (T)H.ps.c_lag, dt = H.ph.dt;
+      const T scale_root = (T)(H.ph.vol / (T)H.ps.theta_prev);
+      const T lo0 = H.ph.lo[0], lo1 = H.ph.lo[1], lo2 = H.ph.lo[2];
+      const T h0 = H.ph.h[0], h1 = H.ph.h[1], h2 = H.ph.h[2];
+      const T hw0 = H.ph.hw[0], hw1 = H.ph.hw[1], hw2 = H.ph.hw[2];
+      const int N0 = H.ph.N[0], N1 = H.ph.N[1], N2 = H.ph.N[2];
+      const int clo0 = H.sd.clo[0], chi0 = H.sd.chi[0], clo1 = H.sd.clo[1], chi1 = H.sd.chi[1];
+      const int clo2 = H.sd.clo[2], chi2 = H.sd.chi[2];
+      const bool want_l2 = H.ph.stop_norm == PMA_STOP_L2_INCREMENT;
+      const bool run = phase == PH_RUN;
+      const bool logrhs = H.ph.rhs == PMA_RHS_LOG || !run;
+      const T inv_dim = T(1) / (T)H.ph.dim;
+      const int nterms = H.ph.mon.nterms;
+      bool fast = (H.ph.mon.kind == PMA_MON_SUM);
+      for (int q = 0; q < kMaxTerms; ++q)
+        if (q < nterms && H.ph.mon.t[q].type != PMA_TERM_BUMP && H.ph.mon.t[q].type != PMA_TERM_RING)
+          fast = false;
+      // column tables after the staged planes
+      T* wcol = sv + SHZ * PS;
+      T* ucol = wcol + cr;
+      T* lcol = ucol + cr;
+      for (int c = tid; c < cr; c += NT) {
+        const int i = i0 + c, gi = g00 + i;
+        const bool valid = c < cols;
+        wcol[c] = (valid && i >= clo0 && i <= chi0) ? ((gi == 0 || gi == N0 - 1) ? hw0 : h0) : T(0);
+        ucol[c] = (valid && i != dlx && i != dhx) ? T(1) : T(0);
+        lcol[c] = (i == 0 || i == n0 - 1) ? hw0 : h0;
+      }
+      __syncthreads();  // box staged
+      P2<T> th2 = P2<T>::s(T(0)), gs2 = P2<T>::s(T(0));
+      T gcmax = -big_val<T>(), gcmin = big_val<T>();
+      const P2<T> NCL = P2<T>::s(-c_lag), DT2 = P2<T>::s(dt);
+      const P2<T> M2 = P2<T>::s(T(-2)), ONE = P2<T>::s(T(1));
+      const P2<T> I2H0 = P2<T>::s(H.ph.inv2h[0]), I2H1 = P2<T>::s(H.ph.inv2h[1]);
+      const P2<T> I2H2 = P2<T>::s(H.ph.inv2h[2]);
+      const P2<T> IH20 = P2<T>::s(H.ph.invh2[0]), IH21 = P2<T>::s(H.ph.invh2[1]);
+      const P2<T> IH22 = P2<T>::s(H.ph.invh2[2]);
+      const P2<T> I4XY = P2<T>::s(H.ph.inv4hh[0]), I4XZ = P2<T>::s(H.ph.inv4hh[1]);
+      const P2<T> I4YZ = P2<T>::s(H.ph.inv4hh[2]);
+      for (int q = tid; q < nruns; q += NT) {
+        const int r = qdiv(q, rpr, inv_rpr), c0 = (q - r * rpr) * 4;
+        const int j = j0 + r, gj = g01 + j;
+        Vec4<T> wc, uc;
+        wc.lds(wcol + c0);
+        uc.lds(ucol + c0);
+        const bool rowdir = (j == dly || j == dhy);
+        const T wyo = (j >= clo1 && j <= chi1) ? ((gj == 0 || gj == N1 - 1) ? hw1 : h1) : T(0);
+        const T xi1 = fma((T)gj, h1, lo1);
+        const int gi0 = g00 + i0 + c0;
+        P2<T> XI0[2];
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp)
+          XI0[pp] = P2<T>::mk(fma((T)(gi0 + 2 * pp), h0, lo0), fma((T)(gi0 + 2 * pp + 1), h0, lo0));
+        for (int l = 0; l < depth; ++l) {
+          const int kk = k0 + l, gk = g02 + kk;
+          const T* p = sv + (l + 1) * PS + (r + 1) * SWp + c0 + 4;
+          // plane z: rows j-1, j, j+1, columns c0-1 .. c0+4
+          T cS[6], cC[6], cN[6];
+          // planes z-1 / z+1: row j (6 columns) and rows j-1, j+1 (4 columns)
+          T dC[6], uC[6];
+          Vec4<T> dS, dN, uS, uN;
+          {
+            Vec4<T> m;
+            cS[0] = p[-SWp - 1]; m.lds(p - SWp); cS[5] = p[-SWp + 4];
+            cS[1] = m.v[0]; cS[2] = m.v[1]; cS[3] = m.v[2]; cS[4] = m.v[3];
+            cC[0] = p[-1]; m.lds(p); cC[5] = p[4];
+            cC[1] = m.v[0]; cC[2] = m.v[1]; cC[3] = m.v[2]; cC[4] = m.v[3];
+            cN[0] = p[SWp - 1]; m.lds(p + SWp); cN[5] = p[SWp + 4];
+            cN[1] = m.v[0]; cN[2] = m.v[1]; cN[3] = m.v[2]; cN[4] = m.v[3];
+            const T* pd = p - PS;
+            dC[0] = pd[-1]; m.lds(pd); dC[5] = pd[4];
+            dC[1] = m.v[0]; dC[2] = m.v[1]; dC[3] = m.v[2]; dC[4] = m.v[3];
+            dS.lds(pd - SWp);
+            dN.lds(pd + SWp);
+            const T* pu = p + PS;
+            uC[0] = pu[-1]; m.lds(pu); uC[5] = pu[4];
+            uC[1] = m.v[0]; uC[2] = m.v[1]; uC[3] = m.v[2]; uC[4] = m.v[3];
+            uS.lds(pu - SWp);
+            uN.lds(pu + SWp);
+          }
+          const bool plndir = (kk == dlz || kk == dhz);
+          const T wzo = (kk >= clo2 && kk <= chi2) ? ((gk == 0 || gk == N2 - 1) ? hw2 : h2) : T(0);
+          const T xi2 = fma((T)gk, h2, lo2);
+          P2<T> X0[2], X1[2], X2[2], DD[2], R[2];
+#pragma unroll
+          for (int pp = 0; pp < 2; ++pp) {
+            const int u0 = 2 * pp;
+            const P2<T> C = P2<T>::mk(cC[u0 + 1], cC[u0 + 2]);
+            const P2<T> E = P2<T>::mk(cC[u0 + 2], cC[u0 + 3]);
+            const P2<T> Wv = P2<T>::mk(cC[u0], cC[u0 + 1]);
+            const P2<T> Nn = P2<T>::mk(cN[u0 + 1], cN[u0 + 2]);
+            const P2<T> Ss = P2<T>::mk(cS[u0 + 1], cS[u0 + 2]);
+            const P2<T> Up = P2<T>::mk(uC[u0 + 1], uC[u0 + 2]);
+            const P2<T> Dn = P2<T>::mk(dC[u0 + 1], dC[u0 + 2]);
+            X0[pp] = pfma(psub(E, Wv), I2H0, XI0[pp]);
+            X1[pp] = pfma(psub(Nn, Ss), I2H1, P2<T>::s(xi1));
+            X2[pp] = pfma(psub(Up, Dn), I2H2, P2<T>::s(xi2));
+            const P2<T> hxx = pfma(pfma(C, M2, padd(E, Wv)), IH20, ONE);
+            const P2<T> hyy = pfma(pfma(C, M2, padd(Nn, Ss)), IH21, ONE);
+            const P2<T> hzz = pfma(pfma(C, M2, padd(Up, Dn)), IH22, ONE);
+            // cross differences (v_{++} - v_{+-}) - (v_{-+} - v_{--})
+            const P2<T> hxy = pmul(psub(psub(P2<T>::mk(cN[u0 + 2], cN[u0 + 3]), P2<T>::mk(cS[u0 + 2], cS[u0 + 3])),
+                                        psub(P2<T>::mk(cN[u0], cN[u0 + 1]), P2<T>::mk(cS[u0], cS[u0 + 1]))),
+                                   I4XY);
+            const P2<T> hxz = pmul(psub(psub(P2<T>::mk(uC[u0 + 2], uC[u0 + 3]), P2<T>::mk(dC[u0 + 2], dC[u0 + 3])),
+                                        psub(P2<T>::mk(uC[u0], uC[u0 + 1]), P2<T>::mk(dC[u0], dC[u0 + 1]))),
+                                   I4XZ);
+            const P2<T> hyz = pmul(psub(psub(P2<T>::mk(uN.v[u0], uN.v[u0 + 1]), P2<T>::mk(uS.v[u0], uS.v[u0 + 1])),
+                                        psub(P2<T>::mk(dN.v[u0], dN.v[u0 + 1]), P2<T>::mk(dS.v[u0], dS.v[u0 + 1]))),
+                                   I4YZ);
+            // det of the symmetric 3x3 matrix by cofactors of the first row
+            const P2<T> m1 = psub(pmul(hyy, hzz), pmul(hyz, hyz));
+            const P2<T> m2 = psub(pmul(hxy, hzz), pmul(hyz, hxz));
+            const P2<T> m3 = psub(pmul(hxy, hyz), pmul(hyy, hxz));
+            DD[pp] = pfma(hxz, m3, psub(pmul(hxx, m1), pmul(hxy, m2)));
+          }
+          if (fast) {
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) R[pp] = P2<T>::s(H.ph.mon.base);
+            for (int k = 0; k < nterms; ++k) {
+              const auto& tm = H.ph.mon.t[k];
+              const P2<T> CX = P2<T>::s(tm.c[0]), CY = P2<T>::s(tm.c[1]), CZ = P2<T>::s(tm.c[2]);
+              const P2<T> R2 = P2<T>::s(tm.r2), NWd = P2<T>::s(-tm.width), AMP = P2<T>::s(tm.amp);
+              const bool ring = tm.type == PMA_TERM_RING;
+#pragma unroll
+              for (int pp = 0; pp < 2; ++pp) {
+                const P2<T> d0 = psub(X0[pp], CX), d1 = psub(X1[pp], CY), d2 = psub(X2[pp], CZ);
+                const P2<T> qq = pfma(d0, d0, pfma(d1, d1, pmul(d2, d2)));
+                const P2<T> s2 = psub(qq, R2);
+                const P2<T> uu = ring ? pmul(s2, s2) : qq;
+                R[pp] = pfma(AMP, pexw<T>(pmul(uu, NWd)), R[pp]);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp)
+              R[pp] = P2<T>::mk(rho_at<T>(H.ph.mon, X0[pp].x(), X1[pp].x(), X2[pp].x()),
+                                rho_at<T>(H.ph.mon, X0[pp].y(), X1[pp].y(), X2[pp].y()));
+          }
+          Vec4<T> o;
+          T gcv[4], rdv[4], dv[4];
+#pragma unroll
+          for (int pp = 0; pp < 2; ++pp) {
+            const P2<T> rD = pmul(R[pp], DD[pp]);
+            P2<T> GC;
+            if (logrhs) {
+              GC = padd(P2<T>::mk(Fm<T>::ln(rD.x()), Fm<T>::ln(rD.y())), NCL);
+            } else {
+              GC = P2<T>::mk(Fm<T>::pw(scale_root * rD.x(), inv_dim) - T(1) - c_lag,
+                             Fm<T>::pw(scale_root * rD.y(), inv_dim) - T(1) - c_lag);
+            }
+            const P2<T> vn = pfma(GC, DT2, P2<T>::mk(cC[2 * pp + 1], cC[2 * pp + 2]));
+            o.v[2 * pp] = vn.x();
+            o.v[2 * pp + 1] = vn.y();
+            gcv[2 * pp] = GC.x();
+            gcv[2 * pp + 1] = GC.y();
+            rdv[2 * pp] = rD.x();
+            rdv[2 * pp + 1] = rD.y();
+            dv[2 * pp] = DD[pp].x();
+            dv[2 * pp + 1] = DD[pp].y();
+          }
+          const T rowu = (rowdir || plndir) ? T(0) : T(1);
+          const T wyz = wyo * wzo;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const bool upd = uc.v[u] * rowu != T(0);
+            gcmax = fmax(gcmax, upd ? gcv[u] : -big_val<T>());
+            gcmin = fmin(gcmin, upd ? gcv[u] : big_val<T>());
+            acc.dmin = fmin(acc.dmin, upd ? dv[u] : big_val<T>());
+            const T g = upd ? gcv[u] : T(0);
+            const T rd = upd ? rdv[u] : T(0);
+            if (u & 1) {
+              gs2 = padd(gs2, P2<T>::mk(T(0), g));
+              th2 = pfma(P2<T>::mk(T(0), wc.v[u] * wyz), P2<T>::mk(T(0), rd), th2);
+            } else {
+              gs2 = padd(gs2, P2<T>::mk(g, T(0)));
+              th2 = pfma(P2<T>::mk(wc.v[u] * wyz, T(0)), P2<T>::mk(rd, T(0)), th2);
+            }
+            if (!upd) o.v[u] = T(0);
+          }
+          if (want_l2) {
+            Vec4<T> lc;
+            lc.lds(lcol + c0);
+            const T wl = ((j == 0 || j == n1 - 1) ? hw1 : h1) * ((kk == 0 || kk == n2 - 1) ? hw2 : h2);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const bool upd = uc.v[u] * rowu != T(0);
+              const T w = upd ? lc.v[u] * wl : T(0);
+              const T d = upd ? gcv[u] : T(0);
+              l2a = fma(w * d, d, l2a);
+              l2b = fma(w, d, l2b);
+              ws += w;
+            }
+          }
+          if (run) {
+            if (rowdir || plndir || (i0 + c0 <= dlx) || (i0 + c0 + 3 >= dhx && dhx >= 0)) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int i = i0 + c0 + u;
+                if (c0 + u < cols && (rowdir || plndir || i == dlx || i == dhx))
+                  o.v[u] = gather_owner<T>(a, H, i, j, kk);
+              }
+            }
+            o.stg(dst + kk * ppitch + j * pitch + i0 + c0);
+          }
+        }
+      }
+      th = th2.x() + th2.y();
+      if (gcmax > -big_val<T>()) acc.gmax = gcmax + c_lag;
+      if (gcmin < big_val<T>()) acc.gmin = gcmin + c_lag;
+      if (!isfinite(gs2.x() + gs2.y())) acc.nf += 1;
     }
-    tile_reduce<T, NT>(th, l2a, l2b, ws, acc, a.part + t, S.w.sub, red_t, red_f, red_i);
+    // tile record
+    th = warp_sum(th);
+    l2a = warp_sum(l2a);
+    l2b = warp_sum(l2b);
+    ws = warp_sum(ws);
+    const T gmax = warp_max(acc.gmax), gmin = warp_min(acc.gmin), dmin = warp_min(acc.dmin);
+    const int nf = warp_isum(acc.nf);
+    if (lane == 0) {
+      red_t[0 * NW + wid] = th;
+      red_t[1 * NW + wid] = l2a;
+      red_t[2 * NW + wid] = l2b;
+      red_t[3 * NW + wid] = ws;
+      red_f[0 * NW + wid] = gmax;
+      red_f[1 * NW + wid] = gmin;
+      red_f[2 * NW + wid] = dmin;
+      red_i[wid] = nf;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      T m0 = -big_val<T>(), m1 = big_val<T>(), m2 = big_val<T>();
+      int cnt = 0;
+      for (int w = 0; w < NW; ++w) {
+        s0 += red_t[0 * NW + w];
+        s1 += red_t[1 * NW + w];
+        s2 += red_t[2 * NW + w];
+        s3 += red_t[3 * NW + w];
+        m0 = fmax(m0, red_f[0 * NW + w]);
+        m1 = fmin(m1, red_f[1 * NW + w]);
+        m2 = fmin(m2, red_f[2 * NW + w]);
+        cnt += red_i[w];
+      }
+      Partial rec;
+      rec.theta = (double)s0;
+      rec.l2a = (double)s1;
+      rec.l2b = (double)s2;
+      rec.wsum = (double)s3;
+      rec.gmax = (double)m0;
+      rec.gmin = (double)m1;
+      rec.dmin = (double)m2;
+      rec.nonfinite = cnt;
+      rec.sub = H.w.sub;
+      a.part[t] = rec;
+    }
   }
   if (tid == 0) queue_exit(a);
 }
@@ -1020,15 +1321,17 @@ __global__ void __launch_bounds__(TX * TY) k_sweep3d(LaunchArgs a) {
 // Compiled shapes.  2D: (threads, band nodes FP32, band nodes FP64); the
 // staged band plus halo is at most 3x the band nodes.  3D: (TX, TY, TZ).
 #define PMA_T2D(X) X(256, 2048, 1024) X(128, 1024, 512) X(256, 1024, 1024) X(512, 3072, 1536)
-#define PMA_T3D(X) X(32, 8, 4) X(32, 4, 8) X(16, 8, 8)
+// 3D: (threads, nodes per plane box, planes FP32, planes FP64, dynamic
+// shared memory in KiB for the staged box and the column tables).
+#define PMA_T3D(X) X(128, 512, 8, 4, 64) X(128, 512, 16, 8, 96) X(256, 1024, 8, 4, 96)
 
 static const int k_t2d[][3] = {
 #define E(a, b, c) {a, b, c},
     PMA_T2D(E)
 #undef E
 };
-static const Tile3D k_t3d[] = {
-#define E(a, b, c) {a, b, c},
+static const int k_t3d[][5] = {
+#define E(a, b, c, d, e) {a, b, c, d, e},
     PMA_T3D(E)
 #undef E
 };
@@ -1046,11 +1349,22 @@ Tile2D tile2d_shape(int id, bool fp64) {
   t.cols = cmax < 1024 ? cmax : 1024;
   return t;
 }
-Tile3D tile3d_shape(int id) { return k_t3d[id]; }
+Tile3D tile3d_shape(int id, bool fp64) {
+  Tile3D t;
+  t.threads = k_t3d[id][0];
+  t.xy = k_t3d[id][1];
+  t.tz = fp64 ? k_t3d[id][3] : k_t3d[id][2];
+  t.smax = k_t3d[id][4] * 1024 / (fp64 ? 8 : 4);
+  // a one-row box: 3 rows x (cols + 8) x (tz + 2) planes + 3 column tables
+  const int cmax = ((t.smax / (3 * (t.tz + 2) + 3)) - 8) & ~3;
+  t.cols = cmax < 1024 ? cmax : 1024;
+  return t;
+}
 
 template <typename T>
-static const void* sweep_fn(int dim, int id, int* nthreads) {
+static const void* sweep_fn(int dim, int id, int* nthreads, int* dyn) {
   int k = 0;
+  *dyn = 0;
   if (dim == 2) {
 #define E(a, b, c)                                                         \
   if (k++ == id) {                                                         \
@@ -1063,10 +1377,14 @@ static const void* sweep_fn(int dim, int id, int* nthreads) {
     PMA_T2D(E)
 #undef E
   } else {
-#define E(a, b, c)                                   \
-  if (k++ == id) {                                   \
-    *nthreads = (a) * (b);                           \
-    return (const void*)k_sweep3d<T, a, b, c>;       \
+#define E(a, b, c, d, e)                                                   \
+  if (k++ == id) {                                                         \
+    *nthreads = (a);                                                       \
+    *dyn = (e) * 1024;                                                     \
+    if constexpr (sizeof(T) == 8)                                          \
+      return (const void*)k_band3d<T, a, d>;                               \
+    else                                                                   \
+      return (const void*)k_band3d<T, a, c>;                               \
   }
     PMA_T3D(E)
 #undef E
@@ -1074,31 +1392,53 @@ static const void* sweep_fn(int dim, int id, int* nthreads) {
   return nullptr;
 }
 
-static const void* cls_fn(int cls, int tile_id, int* nthreads) {
+static const void* cls_fn(int cls, int tile_id, int* nthreads, int* dyn) {
   switch (cls) {
-    case CLS_2D_F32: return sweep_fn<float>(2, tile_id, nthreads);
-    case CLS_2D_F64: return sweep_fn<double>(2, tile_id, nthreads);
-    case CLS_3D_F32: return sweep_fn<float>(3, tile_id, nthreads);
-    case CLS_3D_F64: return sweep_fn<double>(3, tile_id, nthreads);
+    case CLS_2D_F32: return sweep_fn<float>(2, tile_id, nthreads, dyn);
+    case CLS_2D_F64: return sweep_fn<double>(2, tile_id, nthreads, dyn);
+    case CLS_3D_F32: return sweep_fn<float>(3, tile_id, nthreads, dyn);
+    case CLS_3D_F64: return sweep_fn<double>(3, tile_id, nthreads, dyn);
   }
   return nullptr;
 }
 
+// Kernels with dynamic shared memory above 48 KiB must opt in once per
+// function (and device); cheap and idempotent.
+static cudaError_t opt_in(const void* fn, int dyn) {
+  if (dyn <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+}
+
 cudaError_t launch_sweep(int cls, int tile_id, const LaunchArgs& a, cudaStream_t s) {
-  int nt = 0;
-  const void* fn = cls_fn(cls, tile_id, &nt);
+  int nt = 0, dyn = 0;
+  const void* fn = cls_fn(cls, tile_id, &nt, &dyn);
   if (!fn) return cudaErrorInvalidValue;
   if (a.nwork <= 0 || a.grid <= 0) return cudaSuccess;
   void* args[] = {(void*)&a};
-  return cudaLaunchKernel(fn, dim3(a.grid), dim3(nt), args, 0, s);
+  return cudaLaunchKernel(fn, dim3(a.grid), dim3(nt), args, (size_t)dyn, s);
+}
+
+cudaError_t prepare_sweep_kernels() {
+  for (int cls = 0; cls < NUM_CLS; ++cls) {
+    const int n = (cls == CLS_2D_F32 || cls == CLS_2D_F64) ? tile2d_count() : tile3d_count();
+    for (int id = 0; id < n; ++id) {
+      int nt = 0, dyn = 0;
+      const void* fn = cls_fn(cls, id, &nt, &dyn);
+      const cudaError_t e = opt_in(fn, dyn);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 int sweep_max_blocks_per_sm(int cls, int tile_id) {
-  int nt = 0;
-  const void* fn = cls_fn(cls, tile_id, &nt);
+  int nt = 0, dyn = 0;
+  const void* fn = cls_fn(cls, tile_id, &nt, &dyn);
   if (!fn) return 0;
+  if (opt_in(fn, dyn) != cudaSuccess) return 1;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, nt, 0) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, nt, (size_t)dyn) != cudaSuccess)
+    return 1;
   return nb > 0 ? nb : 1;
 }
 
