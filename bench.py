@@ -54,6 +54,74 @@ WORKLOADS = {
 }
 
 
+# ------------------------------------------------------------------ serving
+def serving(args):
+    """Serving stream: Poisson arrivals of mixed 2D / 3D requests submitted
+    from a host thread to a context whose server thread batches them
+    continuously; the same stream on the plain FP64 path (one launch per
+    subdomain and step, no graphs) for comparison."""
+    import torch
+    from paper_2006_14602_gb300 import build, pma
+
+    build.build()
+    pma.load()
+    torch.cuda.init()
+
+    def run(stream, precision, plain):
+        reqs = [(t, p.replace(precision=precision)) for t, p in stream]
+        opts = {"window_steps": args.window, "resident": args.resident}
+        if plain:
+            opts.update(launch_mode=pma.PMA_LAUNCH_PER_SUBDOMAIN, use_graphs=0)
+        with pma.Context(0, 120 << 30, **opts) as ctx:
+            if pma.pma_serve_start(ctx.h) != pma.PMA_OK:
+                raise RuntimeError("server did not start")
+            ids = []
+            t0 = time.perf_counter()
+            for t_arr, p in reqs:
+                d = t0 + t_arr - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                ids.append(ctx.submit(p))
+            lat, nu = [], 0
+            for (_, p), i in zip(reqs, ids):
+                st = pma.pma_wait(ctx.h, i, 600_000_000)
+                if st not in (pma.PMA_OK, pma.PMA_NOT_CONVERGED, pma.PMA_ERR_TANGLED):
+                    raise RuntimeError("request failed: %s" % pma.STATUS_NAMES.get(st, st))
+                _, info = pma.pma_get_info(ctx.h, i)
+                lat.append(info.latency_us / 1e3)
+                nu += info.steps * _sub_nodes(p)
+            wall = time.perf_counter() - t0
+            pma.pma_serve_stop(ctx.h)
+            for i in ids:
+                pma.pma_release(ctx.h, i)
+        return {"meshes_per_s": len(reqs) / wall, "node_updates_per_s": nu / wall,
+                "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99),
+                "wall_s": wall, "requests": len(reqs)}
+
+    stream = W.config5_stream(count=args.requests, rate_hz=args.rate, max_steps=args.max_steps or 2000,
+                              size2d=(33, args.max2d), size3d=(17, args.max3d))
+    warm = W.config5_stream(seed=1, count=4, rate_hz=1e6, max_steps=50, size2d=(33, 65),
+                            size3d=(17, 21))
+    run(warm, "fp32", False)
+    fp32 = run(stream, "fp32", False)
+    plain = run(stream[: args.plain_requests], "fp64", True) if args.plain_requests else None
+    line = {
+        "metric": "meshes/s (serving stream)", "value": fp32["meshes_per_s"], "unit": "meshes/s",
+        "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded Poisson stream, master seed %d)" % W.MASTER_SEED,
+        "config": {"workload": "serving stream: Poisson arrivals at %.1f/s of mixed 2D (33^2-%d^2) "
+                               "and 3D (17^3-%d^3) requests, 1-27 subdomains, random bump "
+                               "monitors, tol 1e-6 or %d steps" % (args.rate, args.max2d,
+                                                                   args.max3d, args.max_steps or 2000),
+                   "requests": len(stream)},
+        "latency_ms": {"p50": fp32["p50_ms"], "p99": fp32["p99_ms"]},
+        "node_updates_per_s": fp32["node_updates_per_s"],
+        "plain_fp64_per_subdomain": plain,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def make_workload(name: str, precision: str, max_steps=None):
     if name == "c4":
         probs = W.config4(precision=precision)
@@ -241,7 +309,7 @@ def native(args, rank, world, device):
     torch.cuda.set_device(device)
     stream = torch.cuda.Stream(device)
     probs = make_workload(args.workload, args.precision, args.max_steps)
-    opts = {"window_steps": args.window}
+    opts = {"window_steps": args.window, "resident": args.resident}
     if args.tile2d is not None:
         opts["tile_2d"] = args.tile2d
     if args.tile3d is not None:
@@ -382,7 +450,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS) + ["c5"])
+    ap.add_argument("--resident", type=int, default=0,
+                    help="k > 0: cluster-resident path for 2D requests that fit the "
+                         "first k shared-memory classes (0: band kernels only)")
+    ap.add_argument("--rate", type=float, default=20.0, help="c5: arrivals per second")
+    ap.add_argument("--requests", type=int, default=64, help="c5: requests in the stream")
+    ap.add_argument("--plain-requests", type=int, default=16,
+                    help="c5: requests of the stream replayed on the plain FP64 path")
+    ap.add_argument("--max2d", type=int, default=513, help="c5: largest 2D side")
+    ap.add_argument("--max3d", type=int, default=65, help="c5: largest 3D side")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--max-steps", type=int, default=None,
                     help="override the per-request step cap (testing only)")
@@ -400,6 +477,8 @@ def main():
         if rank != 0:
             return 0
         return reference_arm(args, world)
+    if args.workload == "c5":
+        return serving(args) if rank == 0 else 0
 
     if world > 1:
         import torch
@@ -436,6 +515,7 @@ def main():
         "data": "synthetic (seeded requests, master seed %d)" % W.MASTER_SEED,
         "config": {"workload": WORKLOADS[args.workload], "requests": len(probs),
                    "precision": args.precision, "window_steps": args.window,
+                   "resident": args.resident,
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "meshes_per_s": a0["meshes"] / (a0["ms"] / 1e3),

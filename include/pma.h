@@ -186,7 +186,9 @@ pma_status pma_create(pma_ctx **ctx, int device, size_t mem_budget_bytes, void *
 /* Stop a running server, wait for the device and free everything. */
 pma_status pma_destroy(pma_ctx *ctx);
 
-/* Tuning knobs (no effect on results).
+/* Tuning knobs.  Window, graphs and admission cap leave results bitwise
+ * unchanged; tile shapes and the resident path change the order in which
+ * theta is summed, so results agree to rounding only.
  *   PMA_OPT_WINDOW_STEPS   steps per CUDA-graph window (default 32)
  *   PMA_OPT_USE_GRAPHS     1 = capture windows in CUDA graphs (default)
  *   PMA_OPT_LAUNCH_MODE    PMA_LAUNCH_BATCHED: all subdomains of all admitted
@@ -195,9 +197,18 @@ pma_status pma_destroy(pma_ctx *ctx);
  *                          one launch per subdomain per step, no graphs
  *   PMA_OPT_TILE_2D        2D tile shape id (0 = auto)
  *   PMA_OPT_TILE_3D        3D tile shape id (0 = auto)
- *   PMA_OPT_MAX_ACTIVE     cap on concurrently admitted requests (0 = none) */
+ *   PMA_OPT_MAX_ACTIVE     cap on concurrently admitted requests (0 = none)
+ *   PMA_OPT_RESIDENT       k > 0: 2D requests of at most 16 subdomains whose
+ *                          subdomains fit the first k shared-memory classes
+ *                          (24, 56, 112, 220 KiB per subdomain) run
+ *                          cluster-resident: one CTA per subdomain for a whole
+ *                          window, transmission values and theta exchanged
+ *                          through distributed shared memory; 0 = band
+ *                          kernels only (default).  Batched launch mode only;
+ *                          decided per request when it is admitted. */
 enum { PMA_OPT_WINDOW_STEPS = 1, PMA_OPT_USE_GRAPHS = 2, PMA_OPT_LAUNCH_MODE = 3,
-       PMA_OPT_TILE_2D = 4, PMA_OPT_TILE_3D = 5, PMA_OPT_MAX_ACTIVE = 6 };
+       PMA_OPT_TILE_2D = 4, PMA_OPT_TILE_3D = 5, PMA_OPT_MAX_ACTIVE = 6,
+       PMA_OPT_RESIDENT = 7 };
 enum { PMA_LAUNCH_BATCHED = 0, PMA_LAUNCH_PER_SUBDOMAIN = 1 };
 pma_status pma_set_option(pma_ctx *ctx, int32_t option, int64_t value);
 pma_status pma_get_option(pma_ctx *ctx, int32_t option, int64_t *value);
@@ -279,9 +290,12 @@ pma_status pma_counts(pma_ctx *ctx, int32_t *queued, int32_t *active, int32_t *f
 /* Counters of the context since creation or the last reset.  window_ms is
  * the device time of the stepping windows, measured with CUDA events on
  * the context's stream around the sweep launches only; node_updates counts
- * subdomain nodes advanced by one step; sweep_bytes is the algorithmic
- * traffic of those updates (one read and one write of v per node);
- * h2d/d2h_bytes are the host<->device copies the context issued.          */
+ * subdomain nodes advanced by one step; sweep_bytes is the algorithmic HBM
+ * traffic of those updates (band kernels: one read and one write of v per
+ * node and step; resident path: one read and one write of v per node and
+ * window); h2d/d2h_bytes are the host<->device copies the context issued;
+ * res_launches and res_node_updates are the resident path's share of
+ * sweep_launches and node_updates.                                        */
 typedef struct {
   int64_t windows;
   int64_t sweep_launches;
@@ -291,6 +305,8 @@ typedef struct {
   double window_ms;
   double h2d_bytes;
   double d2h_bytes;
+  int64_t res_launches;
+  int64_t res_node_updates;
 } pma_stats;
 pma_status pma_get_stats(pma_ctx *ctx, pma_stats *out, int32_t reset);
 

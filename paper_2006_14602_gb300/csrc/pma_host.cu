@@ -74,6 +74,8 @@ struct Request {
   size_t psi_off = 0;
   char* block = nullptr;     // device allocation
   int slot = -1;
+  int res_class = -1;        // resident class, -1: band kernel (fixed at admission)
+  int res_smem = 0;          // shared memory one resident CTA of it needs (max over subs)
   ReqState state = RQ_QUEUED;
   pma_info info{};
   Clock::time_point t_submit, t_done;
@@ -255,6 +257,22 @@ struct pma_ctx {
   bool dirty = true;
   long long dead_tiles = 0, live_tiles = 0;
 
+  // resident path: per precision and class, the CTA table of the packed
+  // clusters; a side stream runs it beside the band kernels
+  struct ResGroup {
+    std::vector<ResCta> h;
+    ResCta* d = nullptr;
+    size_t cap = 0;
+    int nclusters = 0;
+    int smem = 0;
+  };
+  ResGroup rg[2][kResClasses];
+  int res_csize[2][kResClasses] = {};  // cluster size per class (0: unusable)
+  bool res_dirty = true;
+  long long res_packed = 0, res_live = 0;  // subdomain CTAs packed / still running
+  cudaStream_t side[2 * kResClasses] = {};  // one per precision and class
+  cudaEvent_t ev_fork = nullptr, ev_join[2 * kResClasses] = {};
+
   // graphs
   cudaGraphExec_t gexec = nullptr;
   int graph_steps = 0;
@@ -271,6 +289,7 @@ struct pma_ctx {
   int launch_mode = PMA_LAUNCH_BATCHED;
   int opt_tile2d = 0, opt_tile3d = 0;
   int max_active = 0;
+  int opt_resident = 0;
 
   // counters (pma_get_stats)
   pma_stats stats{};
@@ -486,7 +505,8 @@ pma_status rebuild(pma_ctx* c) {
     fill_probdesc(r, pd);
     pd.sub_base = (int)c->h_subs.size();
     std::vector<WorkItem>& wl = c->h_work[r.cls];
-    const bool live = (r.state == RQ_ACTIVE);
+    // resident requests take no band tiles and no finish pass
+    const bool live = (r.state == RQ_ACTIVE) && r.res_class < 0;
     pd.tile_begin = (int)wl.size();
     for (size_t si = 0; si < r.subs.size(); ++si) {
       const HostSub& hs = r.subs[si];
@@ -560,6 +580,136 @@ pma_status rebuild(pma_ctx* c) {
   PMA_CK(cudaStreamSynchronize(c->stream));
   c->dirty = false;
   c->graph_valid = false;
+  c->res_dirty = true;
+  return PMA_OK;
+}
+
+// Resident class of a request (at admission; never changes afterwards, so a
+// request's arithmetic does not depend on what else is admitted): the first
+// class whose shared-memory budget holds every subdomain and whose cluster
+// holds all of them.  -1: the band kernels.
+int pick_res_class(const pma_ctx* c, const Request& r, int* smem) {
+  *smem = 0;
+  if (!c->opt_resident || c->launch_mode != PMA_LAUNCH_BATCHED || r.dim != 2) return -1;
+  if (r.d.transmission != PMA_TRANSMISSION_PARALLEL) return -1;
+  const int nsub = (int)r.subs.size();
+  if (nsub > kResClusterMax) return -1;
+  int need = 0;
+  for (const HostSub& hs : r.subs) {
+    if (hs.n[0] < 4 || hs.n[1] < 4) return -1;
+    need = std::max(need, res_smem_bytes(hs.n[0], hs.n[1], r.esize));
+  }
+  const int f = r.esize == 8 ? 1 : 0;
+  const int nclass = std::min(c->opt_resident, kResClasses);
+  for (int id = 0; id < nclass; ++id)
+    if (need <= res_class(id, f == 1).smem_bytes && nsub <= c->res_csize[f][id]) {
+      *smem = need;
+      return id;
+    }
+  return -1;
+}
+
+// Pack the active resident requests of every class into clusters (first fit
+// over requests by decreasing subdomain count; the CTAs of one request are
+// consecutive ranks of one cluster, in subdomain order).
+pma_status rebuild_res(pma_ctx* c) {
+  for (int f = 0; f < 2; ++f)
+    for (int id = 0; id < kResClasses; ++id) {
+      pma_ctx::ResGroup& g = c->rg[f][id];
+      g.h.clear();
+      g.nclusters = 0;
+      g.smem = 0;
+    }
+  c->res_packed = c->res_live = 0;
+  std::vector<const Request*> rs;
+  for (uint64_t id : c->active) {
+    const Request& r = *c->reqs[id];
+    if (r.res_class >= 0 && c->h_state[r.slot].phase != PH_DONE) rs.push_back(&r);
+  }
+  std::stable_sort(rs.begin(), rs.end(), [](const Request* a, const Request* b) {
+    return a->subs.size() > b->subs.size();
+  });
+  std::vector<int> fill[2][kResClasses];
+  for (const Request* rp : rs) {
+    const Request& r = *rp;
+    const int f = r.esize == 8 ? 1 : 0, id = r.res_class;
+    const int cs = c->res_csize[f][id], nsub = (int)r.subs.size();
+    pma_ctx::ResGroup& g = c->rg[f][id];
+    std::vector<int>& fl = fill[f][id];
+    int bin = -1;
+    for (size_t b = 0; b < fl.size(); ++b)
+      if (fl[b] + nsub <= cs) {
+        bin = (int)b;
+        break;
+      }
+    if (bin < 0) {
+      bin = (int)fl.size();
+      fl.push_back(0);
+      g.h.resize((size_t)cs * fl.size(), ResCta{-1, 0, {0, 0}});
+    }
+    const int rank0 = fl[bin];
+    const int base = c->h_probs[r.slot].sub_base;
+    for (int s2 = 0; s2 < nsub; ++s2) g.h[(size_t)bin * cs + rank0 + s2] = ResCta{base + s2, rank0, {0, 0}};
+    fl[bin] += nsub;
+    g.smem = std::max(g.smem, r.res_smem);
+    c->res_packed += nsub;
+  }
+  c->res_live = c->res_packed;
+  for (int f = 0; f < 2; ++f)
+    for (int id = 0; id < kResClasses; ++id) {
+      pma_ctx::ResGroup& g = c->rg[f][id];
+      const int cs = c->res_csize[f][id];
+      g.nclusters = cs > 0 ? (int)(g.h.size() / cs) : 0;
+      if (g.h.empty()) continue;
+      pma_status st = ensure_buf(&g.d, &g.cap, g.h.size());
+      if (st != PMA_OK) return st;
+      PMA_CK(cudaMemcpyAsync(g.d, g.h.data(), sizeof(ResCta) * g.h.size(),
+                             cudaMemcpyHostToDevice, c->stream));
+      c->stats.h2d_bytes += (double)sizeof(ResCta) * g.h.size();
+    }
+  PMA_CK(cudaStreamSynchronize(c->stream));
+  c->res_dirty = false;
+  return PMA_OK;
+}
+
+int res_launches(const pma_ctx* c) {
+  int n = 0;
+  for (int f = 0; f < 2; ++f)
+    for (int id = 0; id < kResClasses; ++id) n += c->rg[f][id].nclusters > 0 ? 1 : 0;
+  return n;
+}
+
+// One window of the resident path: one launch per precision and class, each
+// on its own stream so that they run side by side (ordered after everything
+// already on the context's stream, which waits for all of them).
+pma_status launch_res_window(pma_ctx* c, int steps) {
+  PMA_CK(cudaEventRecord(c->ev_fork, c->stream));
+  for (int f = 0; f < 2; ++f)
+    for (int id = 0; id < kResClasses; ++id) {
+      const pma_ctx::ResGroup& g = c->rg[f][id];
+      if (g.nclusters == 0) continue;
+      cudaStream_t ss = c->side[f * kResClasses + id];
+      PMA_CK(cudaStreamWaitEvent(ss, c->ev_fork, 0));
+      ResArgs a;
+      a.hotf = c->d_hotf;
+      a.hotd = c->d_hotd;
+      a.ctas = g.d;
+      a.subs = c->d_subs;
+      a.probs = c->d_probs;
+      a.st = c->d_state;
+      a.iters = steps;
+      a.pad = 0;
+      PMA_CK(launch_res2d(f == 1, id, a, g.nclusters, c->res_csize[f][id], g.smem, ss));
+      PMA_CK(cudaEventRecord(c->ev_join[f * kResClasses + id], ss));
+    }
+  return PMA_OK;
+}
+
+pma_status join_res_window(pma_ctx* c) {
+  for (int f = 0; f < 2; ++f)
+    for (int id = 0; id < kResClasses; ++id)
+      if (c->rg[f][id].nclusters > 0)
+        PMA_CK(cudaStreamWaitEvent(c->stream, c->ev_join[f * kResClasses + id], 0));
   return PMA_OK;
 }
 
@@ -619,9 +769,21 @@ pma_status run_window(pma_ctx* c, int steps) {
     pma_status st = rebuild(c);
     if (st != PMA_OK) return st;
   }
+  if (c->res_dirty) {
+    pma_status st = rebuild_res(c);
+    if (st != PMA_OK) return st;
+  }
   const bool graphs = c->use_graphs && c->launch_mode == PMA_LAUNCH_BATCHED;
+  const int nres = res_launches(c);
+  const int nband = launches_per_step(c);
   PMA_CK(cudaEventRecord(c->ev0, c->stream));
-  if (graphs) {
+  if (nres > 0) {
+    pma_status st = launch_res_window(c, steps);
+    if (st != PMA_OK) return st;
+  }
+  if (nband == 0) {
+    // resident work only
+  } else if (graphs) {
     if (!c->graph_valid || c->graph_steps != steps) {
       if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
@@ -650,6 +812,10 @@ pma_status run_window(pma_ctx* c, int steps) {
       if (st != PMA_OK) return st;
     }
   }
+  if (nres > 0) {
+    pma_status st = join_res_window(c);
+    if (st != PMA_OK) return st;
+  }
   PMA_CK(cudaEventRecord(c->ev1, c->stream));
   PMA_CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(ProbState) * c->slot_cap,
                          cudaMemcpyDeviceToHost, c->stream));
@@ -658,7 +824,8 @@ pma_status run_window(pma_ctx* c, int steps) {
   PMA_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   c->stats.windows += 1;
   c->stats.window_ms += ms;
-  c->stats.sweep_launches += (int64_t)steps * launches_per_step(c);
+  c->stats.sweep_launches += (int64_t)steps * nband + nres;
+  c->stats.res_launches += nres;
   c->stats.d2h_bytes += (double)sizeof(ProbState) * c->slot_cap;
   return PMA_OK;
 }
@@ -671,6 +838,7 @@ void collect(pma_ctx* c) {
     Request& r = *c->reqs[id];
     const ProbState& ps = c->h_state[r.slot];
     if (ps.phase == PH_DONE) {
+      if (r.res_class >= 0) c->res_live -= (long long)r.subs.size();
       r.state = RQ_FINISHED;
       r.t_done = now;
       r.info.steps = ps.step;
@@ -694,6 +862,8 @@ void collect(pma_ctx* c) {
       live += pd.tile_end - pd.tile_begin;
     }
     if (live * 2 < c->live_tiles) c->dirty = true;
+    // repack the clusters when most resident CTAs idle
+    if (c->res_live * 2 < c->res_packed) c->res_dirty = true;
     c->active.swap(still);
     c->cv.notify_all();
   }
@@ -726,6 +896,7 @@ pma_status admit(pma_ctx* c) {
     }
     r.slot = c->free_slots.back();
     c->free_slots.pop_back();
+    r.res_class = pick_res_class(c, r, &r.res_smem);
     ProbState ps{};
     ps.phase = PH_INIT_V;
     ps.status = PMA_PENDING;
@@ -773,9 +944,10 @@ pma_status combine_into(pma_ctx* c, Request& r, void* x, int out_fp64, void* psi
   }
   pma_status st = ensure_jobs(c, 1);
   if (st != PMA_OK) return st;
-  CombineJob j{r.slot, out_fp64, x, psi};
+  CombineJob j{r.slot, out_fp64, x, psi, 0};
+  const long long nb = (r.nodes + kCombineNodes - 1) / kCombineNodes;
   PMA_CK(cudaMemcpyAsync(c->d_jobs, &j, sizeof(j), cudaMemcpyHostToDevice, c->stream));
-  PMA_CK(launch_combine(c->d_jobs, 1, r.nodes, c->d_subs, c->d_probs, c->d_state, c->stream));
+  PMA_CK(launch_combine(c->d_jobs, 1, nb, c->d_subs, c->d_probs, c->d_state, c->stream));
   // the job record lives on this stack frame: wait for the copy
   PMA_CK(cudaStreamSynchronize(c->stream));
   c->stats.h2d_bytes += sizeof(j);
@@ -798,7 +970,12 @@ pma_status loop_once(pma_ctx* c, std::unique_lock<std::mutex>& lk, bool* idle) {
     const Request& r = *c->reqs[ids[i]];
     const long long d = c->h_state[r.slot].step - before[i];
     c->stats.node_updates += d * r.sub_nodes;
-    c->stats.sweep_bytes += 2.0 * r.esize * (double)(d * r.sub_nodes);
+    if (r.res_class >= 0) {
+      c->stats.res_node_updates += d * r.sub_nodes;
+      c->stats.sweep_bytes += 2.0 * r.esize * (double)r.sub_nodes;
+    } else {
+      c->stats.sweep_bytes += 2.0 * r.esize * (double)(d * r.sub_nodes);
+    }
   }
   collect(c);
   (void)lk;
@@ -845,6 +1022,23 @@ pma_status pma_create(pma_ctx** out, int device, size_t mem_budget_bytes, void* 
   }
   c->budget = mem_budget_bytes;
   PMA_CK(prepare_sweep_kernels());
+  PMA_CK(prepare_res_kernels());
+  // largest cluster (16, else 8, 4) each resident class can launch at its
+  // full budget on this device
+  for (int f = 0; f < 2; ++f)
+    for (int id = 0; id < kResClasses; ++id) {
+      c->res_csize[f][id] = 0;
+      for (int cs = kResClusterMax; cs >= 4; cs /= 2)
+        if (res_max_clusters(f == 1, id, cs, res_class(id, f == 1).smem_bytes) > 0) {
+          c->res_csize[f][id] = cs;
+          break;
+        }
+    }
+  for (int k = 0; k < 2 * kResClasses; ++k) {
+    PMA_CK(cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking));
+    PMA_CK(cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming));
+  }
+  PMA_CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   pma_status st = ensure_slots(c.get(), 64);
   if (st != PMA_OK) return st;
   PMA_CK(cudaMalloc(&c->d_check, sizeof(double) * 4 + sizeof(unsigned long long)));
@@ -881,6 +1075,16 @@ pma_status pma_destroy(pma_ctx* c) {
   cudaFree(c->d_queue);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  for (int f = 0; f < 2; ++f)
+    for (int id = 0; id < kResClasses; ++id) cudaFree(c->rg[f][id].d);
+  for (int k = 0; k < 2 * kResClasses; ++k) {
+    if (c->side[k]) {
+      cudaStreamSynchronize(c->side[k]);
+      cudaStreamDestroy(c->side[k]);
+    }
+    if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return PMA_OK;
@@ -913,6 +1117,10 @@ pma_status pma_set_option(pma_ctx* c, int32_t opt, int64_t v) {
       if (v < 0) return PMA_ERR_INVALID;
       c->max_active = (int)v;
       break;
+    case PMA_OPT_RESIDENT:
+      if (v < 0) return PMA_ERR_INVALID;
+      c->opt_resident = (int)std::min<int64_t>(v, kResClasses);
+      break;
     default: return PMA_ERR_INVALID;
   }
   c->graph_valid = false;
@@ -929,6 +1137,7 @@ pma_status pma_get_option(pma_ctx* c, int32_t opt, int64_t* v) {
     case PMA_OPT_TILE_2D: *v = c->opt_tile2d; break;
     case PMA_OPT_TILE_3D: *v = c->opt_tile3d; break;
     case PMA_OPT_MAX_ACTIVE: *v = c->max_active; break;
+    case PMA_OPT_RESIDENT: *v = c->opt_resident; break;
     default: return PMA_ERR_INVALID;
   }
   return PMA_OK;
@@ -1222,15 +1431,15 @@ pma_status pma_get_mesh_device_batch(pma_ctx* c, int32_t n, const uint64_t* ids,
   std::lock_guard<std::mutex> lk(c->mu);
   PMA_CK(cudaSetDevice(c->device));
   std::vector<CombineJob> jobs;
-  long long maxn = 0;
+  long long blocks = 0;
   for (int i = 0; i < n; ++i) {
     auto it = c->reqs.find(ids[i]);
     if (it == c->reqs.end()) return PMA_ERR_NOT_FOUND;
     Request& r = *it->second;
     if (r.state != RQ_FINISHED || !r.block) return PMA_ERR_BUSY;
     if (!x_dev[i]) return PMA_ERR_INVALID;
-    jobs.push_back(CombineJob{r.slot, out_fp64 ? 1 : 0, x_dev[i], nullptr});
-    maxn = std::max(maxn, r.nodes);
+    jobs.push_back(CombineJob{r.slot, out_fp64 ? 1 : 0, x_dev[i], nullptr, blocks});
+    blocks += (r.nodes + kCombineNodes - 1) / kCombineNodes;
   }
   if (jobs.empty()) return PMA_OK;
   if (c->dirty) {
@@ -1241,7 +1450,7 @@ pma_status pma_get_mesh_device_batch(pma_ctx* c, int32_t n, const uint64_t* ids,
   if (st != PMA_OK) return st;
   PMA_CK(cudaMemcpyAsync(c->d_jobs, jobs.data(), sizeof(CombineJob) * jobs.size(),
                          cudaMemcpyHostToDevice, c->stream));
-  PMA_CK(launch_combine(c->d_jobs, (int)jobs.size(), maxn, c->d_subs, c->d_probs, c->d_state,
+  PMA_CK(launch_combine(c->d_jobs, (int)jobs.size(), blocks, c->d_subs, c->d_probs, c->d_state,
                         c->stream));
   PMA_CK(cudaStreamSynchronize(c->stream));
   c->stats.h2d_bytes += (double)sizeof(CombineJob) * jobs.size();
@@ -1457,9 +1666,11 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   }
 
   // owner-takes combination into the caller's buffer
-  const CombineJob job{0, 1, x_dev, nullptr};
+  const CombineJob job{0, 1, x_dev, nullptr, 0};
   PMA_CK(cudaMemcpyAsync(B + o_job, &job, sizeof(job), cudaMemcpyHostToDevice, s));
-  PMA_CK(launch_combine((const CombineJob*)(B + o_job), 1, r.nodes, la.subs, la.probs, la.st, s));
+  PMA_CK(launch_combine((const CombineJob*)(B + o_job), 1,
+                        (r.nodes + kCombineNodes - 1) / kCombineNodes, la.subs, la.probs, la.st,
+                        s));
   PMA_CK(cudaStreamSynchronize(s));
   if (info) {
     info->steps = ps.step;

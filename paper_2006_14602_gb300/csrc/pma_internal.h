@@ -147,6 +147,57 @@ struct Tile2D { int threads, nodes, smax, cols; };
 // 3D: a box of at most `xy` nodes per plane (cols x rows) over `tz` planes.
 struct Tile3D { int threads, xy, tz, smax, cols; };
 
+// Cluster-resident 2D path.  A thread-block cluster of up to 16 CTAs holds
+// the subdomains of one or more problems, one subdomain per CTA, in shared
+// memory for a whole window of steps; transmission values are read from the
+// owner's shared memory (distributed shared memory) and theta is reduced
+// across the problem's CTAs once per step.  Problems are packed into
+// clusters on the host; a CTA without a subdomain only takes part in the
+// cluster barriers.
+struct ResCta {
+  int sub;    // subdomain table index, -1: idle CTA
+  int rank0;  // cluster rank of the CTA holding subdomain 0 of the problem
+  int pad[2];
+};
+
+struct ResArgs {
+  const ProbHot<float>* hotf;
+  const ProbHot<double>* hotd;
+  const ResCta* ctas;  // one entry per CTA of the launch
+  const SubDesc* subs;
+  const ProbDesc* probs;
+  ProbState* st;
+  int iters;  // steps of this launch
+  int pad;
+};
+
+// Shared-memory layout of one resident CTA: two state buffers of
+// res_cap_elems() elements (rows of n0 rounded up to 4 plus 8 halo/padding
+// columns, n1 + 2 rows), the three column tables, the transmission list (at
+// most the subdomain's ring plus 8 mirror images, 8 bytes each) and one
+// saved value per list entry.
+__host__ __device__ inline int res_cap_elems(int n0, int n1) {
+  const int swp = ((n0 + 3) & ~3) + 8;
+  return ((n1 + 2) * swp + 3) & ~3;
+}
+__host__ __device__ inline int res_smem_bytes(int n0, int n1, int esize) {
+  const int cr = (n0 + 3) & ~3;
+  const int ndir = 2 * (n0 + n1) + 8;
+  return (2 * res_cap_elems(n0, n1) + 3 * cr) * esize + ndir * (8 + esize);
+}
+
+// Resident classes: shared-memory budget and threads per CTA.
+struct ResClass { int smem_bytes, threads; };
+constexpr int kResClasses = 4;
+constexpr int kResClusterMax = 16;
+ResClass res_class(int id, bool fp64);
+cudaError_t prepare_res_kernels();
+// Clusters of `csize` CTAs of class `id` that fit on the device at once (0:
+// the shape cannot be launched).
+int res_max_clusters(bool fp64, int id, int csize, int smem_bytes);
+cudaError_t launch_res2d(bool fp64, int id, const ResArgs& a, int nclusters, int csize,
+                         int smem_bytes, cudaStream_t s);
+
 // Kernel launch entry points (pma_kernels.cu).
 struct LaunchArgs {
   const ProbHot<float>* hotf;
@@ -179,13 +230,18 @@ cudaError_t prepare_sweep_kernels();
 cudaError_t launch_finish(const int* list, int n, const SubDesc* subs, const ProbDesc* probs,
                           ProbState* st, const Partial* part, cudaStream_t s);
 
+// One combination job: a request's global mesh.  Jobs are laid out on a
+// flat grid of blocks of kCombineNodes nodes; block_begin is the job's first
+// block (prefix sum over the jobs).
+constexpr int kCombineNodes = 1024;
 struct CombineJob {
   int prob;        // slot
   int out_fp64;
   void* x;         // dim * N values
   void* psi;       // optional N values
+  long long block_begin;
 };
-cudaError_t launch_combine(const CombineJob* jobs_dev, int njobs, long long max_nodes,
+cudaError_t launch_combine(const CombineJob* jobs_dev, int njobs, long long total_blocks,
                            const SubDesc* subs, const ProbDesc* probs, const ProbState* st,
                            cudaStream_t s);
 

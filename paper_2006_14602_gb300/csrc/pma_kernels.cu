@@ -25,6 +25,7 @@
 
 #include <cfloat>
 #include <cstdint>
+#include <cstring>
 
 #include "pma_device.cuh"
 #include "pma_internal.h"
@@ -177,6 +178,59 @@ __device__ __forceinline__ double warp_dsum(double v) {
   return v;
 }
 
+// State advance after the theta^0 pass (Sect. 4.4: c^0 from theta^0; the
+// lagged constant starts equal to it, so the first step carries no offset).
+__device__ __forceinline__ void advance_init(ProbState* ps, double theta, double c_n, double dm,
+                                             bool tangled, long long max_steps) {
+  ps->theta = theta;
+  ps->theta_prev = theta;
+  ps->c_lag = c_n;
+  ps->corr = 0.0;
+  ps->shift = 0.0;
+  ps->min_det = dm;
+  if (tangled) {
+    ps->status = PMA_ERR_TANGLED;
+    ps->phase = PH_DONE;
+  } else if (max_steps <= 0) {
+    ps->status = PMA_NOT_CONVERGED;
+    ps->phase = PH_DONE;
+  } else {
+    ps->phase = PH_RUN;
+  }
+}
+
+// State advance after a forward-Euler step: the stop test of Eq.
+// (dd_stop_criterion) every check_every steps, the step cap, and tangling
+// (the state read by the step is kept).  Transmission nodes written by the
+// step carry the old normalisation offset: corr = dt (c^n - c^{n-1}).
+__device__ __forceinline__ void advance_run(ProbState* ps, double theta, double c_n, double dm,
+                                            bool tangled, double r, double dt, int check_every,
+                                            double tol, long long max_steps) {
+  ps->theta = theta;
+  ps->min_det = dm;
+  if (tangled) {
+    ps->status = PMA_ERR_TANGLED;
+    ps->phase = PH_DONE;
+    return;
+  }
+  ps->residual = r;
+  const double corr = dt * (c_n - ps->c_lag);
+  ps->corr = corr;
+  ps->shift += corr;
+  ps->c_lag = c_n;
+  ps->theta_prev = theta;
+  ps->parity ^= 1;
+  const long long step = ps->step + 1;
+  ps->step = step;
+  if ((step % check_every) == 0 && r <= tol) {
+    ps->status = PMA_OK;
+    ps->phase = PH_DONE;
+  } else if (step >= max_steps) {
+    ps->status = PMA_NOT_CONVERGED;
+    ps->phase = PH_DONE;
+  }
+}
+
 __global__ void k_finish(const int* __restrict__ list, int n, const SubDesc* __restrict__ subs,
                          const ProbDesc* __restrict__ probs, ProbState* st,
                          const Partial* __restrict__ part) {
@@ -215,23 +269,7 @@ __global__ void k_finish(const int* __restrict__ list, int n, const SubDesc* __r
   if (pd.rhs == PMA_RHS_LOG && pd.normalize == PMA_NORM_GLOBAL_THETA) c_n = log(theta / pd.vol);
   const bool tangled = nf > 0 || !(dm > 0.0) || !isfinite(theta);
   if (phase == PH_INIT_THETA) {
-    if (lane == 0) {
-      ps->theta = theta;
-      ps->theta_prev = theta;
-      ps->c_lag = c_n;
-      ps->corr = 0.0;
-      ps->shift = 0.0;
-      ps->min_det = dm;
-      if (tangled) {
-        ps->status = PMA_ERR_TANGLED;
-        ps->phase = PH_DONE;
-      } else if (pd.max_steps <= 0) {
-        ps->status = PMA_NOT_CONVERGED;
-        ps->phase = PH_DONE;
-      } else {
-        ps->phase = PH_RUN;
-      }
-    }
+    if (lane == 0) advance_init(ps, theta, c_n, dm, tangled, pd.max_steps);
     return;
   }
   // residual: per subdomain, combined by the stop rule (max = ALL, min = ANY)
@@ -271,32 +309,8 @@ __global__ void k_finish(const int* __restrict__ list, int n, const SubDesc* __r
       r = any ? fmin(r, r_s) : fmax(r, r_s);
     }
   }
-  if (lane == 0) {
-    ps->theta = theta;
-    ps->min_det = dm;
-    if (tangled) {
-      ps->status = PMA_ERR_TANGLED;
-      ps->phase = PH_DONE;
-    } else {
-      ps->residual = r;
-      // transmission nodes written this step carry the old offset
-      const double corr = pd.dt * (c_n - c_lag);
-      ps->corr = corr;
-      ps->shift += corr;
-      ps->c_lag = c_n;
-      ps->theta_prev = theta;
-      ps->parity ^= 1;
-      const long long step = ps->step + 1;
-      ps->step = step;
-      if ((step % pd.check_every) == 0 && r <= pd.tol) {
-        ps->status = PMA_OK;
-        ps->phase = PH_DONE;
-      } else if (step >= pd.max_steps) {
-        ps->status = PMA_NOT_CONVERGED;
-        ps->phase = PH_DONE;
-      }
-    }
-  }
+  if (lane == 0)
+    advance_run(ps, theta, c_n, dm, tangled, r, pd.dt, pd.check_every, pd.tol, pd.max_steps);
 }
 
 cudaError_t launch_finish(const int* list, int n, const SubDesc* subs, const ProbDesc* probs,
@@ -417,6 +431,9 @@ struct Vec4<float> {
     asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v[0]), "f"(v[1]),
                  "f"(v[2]), "f"(v[3]));
   }
+  __device__ __forceinline__ void sts(float* p) const {
+    *(float4*)p = make_float4(v[0], v[1], v[2], v[3]);
+  }
 };
 template <>
 struct Vec4<double> {
@@ -428,6 +445,10 @@ struct Vec4<double> {
   __device__ __forceinline__ void stg(double* p) const {
     asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(v[0]), "d"(v[1]));
     asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p + 2), "d"(v[2]), "d"(v[3]));
+  }
+  __device__ __forceinline__ void sts(double* p) const {
+    *(double2*)p = make_double2(v[0], v[1]);
+    *(double2*)(p + 2) = make_double2(v[2], v[3]);
   }
 };
 
@@ -476,6 +497,195 @@ __device__ __forceinline__ P2<T> pexw(P2<T> a) {
 template <typename T>
 __device__ __forceinline__ void copy16(T* d, const T* s) {
   *(int4*)d = __ldcg((const int4*)s);
+}
+
+// ---------------------------------------------------------------- 2D stencil
+// Loop invariants of one 2D subdomain (or band) for one step, in registers.
+template <typename T>
+struct RunK {
+  P2<T> NCL, DT2, M2, ONE, I2H0, I2H1, IH20, IH21, INV4, NINV4;
+  T c_lag, scale_root, inv_dim, lo0, h0, lo1, h1;
+  int nterms;
+  bool fast, logrhs, want_l2;
+};
+
+template <typename T>
+__device__ __forceinline__ RunK<T> make_runk(const ProbHot<T>& ph, const ProbState& ps, int phase) {
+  RunK<T> K;
+  K.c_lag = (T)ps.c_lag;
+  K.scale_root = (T)(ph.vol / (T)ps.theta_prev);
+  K.inv_dim = T(1) / (T)ph.dim;
+  K.lo0 = ph.lo[0];
+  K.lo1 = ph.lo[1];
+  K.h0 = ph.h[0];
+  K.h1 = ph.h[1];
+  K.NCL = P2<T>::s(-K.c_lag);
+  K.DT2 = P2<T>::s(ph.dt);
+  K.M2 = P2<T>::s(T(-2));
+  K.ONE = P2<T>::s(T(1));
+  K.I2H0 = P2<T>::s(ph.inv2h[0]);
+  K.I2H1 = P2<T>::s(ph.inv2h[1]);
+  K.IH20 = P2<T>::s(ph.invh2[0]);
+  K.IH21 = P2<T>::s(ph.invh2[1]);
+  K.INV4 = P2<T>::s(ph.inv4hh[0]);
+  K.NINV4 = P2<T>::s(-ph.inv4hh[0]);
+  K.want_l2 = ph.stop_norm == PMA_STOP_L2_INCREMENT;
+  K.logrhs = ph.rhs == PMA_RHS_LOG || phase != PH_RUN;
+  K.nterms = ph.mon.nterms;
+  bool fast = (ph.mon.kind == PMA_MON_SUM);
+  for (int q = 0; q < kMaxTerms; ++q)
+    if (q < K.nterms && ph.mon.t[q].type != PMA_TERM_BUMP && ph.mon.t[q].type != PMA_TERM_RING)
+      fast = false;
+  K.fast = fast;
+  return K;
+}
+
+// Partial sums of one thread: theta (owned nodes), sum of G - c over updated
+// nodes (a non-finite value anywhere makes it non-finite), extrema of G - c,
+// min det, and the L2-increment pieces.
+template <typename T>
+struct RunAcc {
+  P2<T> th2, gs2;
+  T gcmax, gcmin, dmin, l2a, l2b, ws;
+  __device__ __forceinline__ static RunAcc zero() {
+    RunAcc a;
+    a.th2 = P2<T>::s(T(0));
+    a.gs2 = P2<T>::s(T(0));
+    a.gcmax = -big_val<T>();
+    a.gcmin = big_val<T>();
+    a.dmin = big_val<T>();
+    a.l2a = a.l2b = a.ws = T(0);
+    return a;
+  }
+};
+
+// One run of 4 consecutive x-nodes of a row (Eqs. pmae2d, pmae): reads the
+// 3 x 6 window around p (the first node of the run in a shared array of row
+// stride SWp, with valid halo columns and rows), forms x = grad_h Psi,
+// det D_h^2 Psi, rho(x) and G - c_lag, and returns v + dt (G - c_lag) in o
+// (0 at nodes that are not updated: wc/uc/lc are the run's entries of the
+// column tables, rowdir marks a transmission row).
+template <typename T>
+__device__ __forceinline__ void stencil_run4(const RunK<T>& K, const MonT<T>& mon, const T* p,
+                                             int SWp, const T* wcp, const T* ucp, const T* lcp,
+                                             bool rowdir, T wyo, T wly, T xi1, int gi0,
+                                             Vec4<T>& o, RunAcc<T>& A) {
+  // 3 x 6 window: columns c0-1 .. c0+4 of rows j-1, j, j+1
+  T wS[6], wC[6], wN[6];
+  {
+    Vec4<T> m;
+    wS[0] = p[-SWp - 1];
+    m.lds(p - SWp);
+    wS[1] = m.v[0]; wS[2] = m.v[1]; wS[3] = m.v[2]; wS[4] = m.v[3];
+    wS[5] = p[-SWp + 4];
+    wC[0] = p[-1];
+    m.lds(p);
+    wC[1] = m.v[0]; wC[2] = m.v[1]; wC[3] = m.v[2]; wC[4] = m.v[3];
+    wC[5] = p[4];
+    wN[0] = p[SWp - 1];
+    m.lds(p + SWp);
+    wN[1] = m.v[0]; wN[2] = m.v[1]; wN[3] = m.v[2]; wN[4] = m.v[3];
+    wN[5] = p[SWp + 4];
+  }
+  Vec4<T> wc, uc;
+  wc.lds(wcp);
+  uc.lds(ucp);
+  const P2<T> dA = psub(P2<T>::mk(wN[0], wN[1]), P2<T>::mk(wS[0], wS[1]));
+  const P2<T> dB = psub(P2<T>::mk(wN[2], wN[3]), P2<T>::mk(wS[2], wS[3]));
+  const P2<T> dC = psub(P2<T>::mk(wN[4], wN[5]), P2<T>::mk(wS[4], wS[5]));
+  P2<T> X0[2], X1[2], DD[2], R[2];
+#pragma unroll
+  for (int pp = 0; pp < 2; ++pp) {
+    const P2<T> C = P2<T>::mk(wC[2 * pp + 1], wC[2 * pp + 2]);
+    const P2<T> E = P2<T>::mk(wC[2 * pp + 2], wC[2 * pp + 3]);
+    const P2<T> Wv = P2<T>::mk(wC[2 * pp], wC[2 * pp + 1]);
+    const P2<T> Nn = P2<T>::mk(wN[2 * pp + 1], wN[2 * pp + 2]);
+    const P2<T> Ss = P2<T>::mk(wS[2 * pp + 1], wS[2 * pp + 2]);
+    const P2<T> XI0 = P2<T>::mk(fma((T)(gi0 + 2 * pp), K.h0, K.lo0),
+                                fma((T)(gi0 + 2 * pp + 1), K.h0, K.lo0));
+    X0[pp] = pfma(psub(E, Wv), K.I2H0, XI0);
+    X1[pp] = pfma(psub(Nn, Ss), K.I2H1, P2<T>::s(xi1));
+    const P2<T> hxx = pfma(pfma(C, K.M2, padd(E, Wv)), K.IH20, K.ONE);
+    const P2<T> hyy = pfma(pfma(C, K.M2, padd(Nn, Ss)), K.IH21, K.ONE);
+    const P2<T> df = pp == 0 ? psub(dB, dA) : psub(dC, dB);
+    DD[pp] = pfma(pmul(df, K.INV4), pmul(df, K.NINV4), pmul(hxx, hyy));
+  }
+  if (K.fast) {
+    // sum of Gaussian bumps / rings, two nodes per operation
+#pragma unroll
+    for (int pp = 0; pp < 2; ++pp) R[pp] = P2<T>::s(mon.base);
+    for (int k = 0; k < K.nterms; ++k) {
+      const auto& tm = mon.t[k];
+      const P2<T> CX = P2<T>::s(tm.c[0]), CY = P2<T>::s(tm.c[1]), R2 = P2<T>::s(tm.r2);
+      const P2<T> NWd = P2<T>::s(-tm.width), AMP = P2<T>::s(tm.amp);
+      const bool ring = tm.type == PMA_TERM_RING;
+#pragma unroll
+      for (int pp = 0; pp < 2; ++pp) {
+        const P2<T> d0 = psub(X0[pp], CX), d1 = psub(X1[pp], CY);
+        const P2<T> qq = pfma(d0, d0, pmul(d1, d1));
+        const P2<T> s2 = psub(qq, R2);
+        const P2<T> uu = ring ? pmul(s2, s2) : qq;
+        R[pp] = pfma(AMP, pexw<T>(pmul(uu, NWd)), R[pp]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int pp = 0; pp < 2; ++pp)
+      R[pp] = P2<T>::mk(rho_at<T>(mon, X0[pp].x(), X1[pp].x(), T(0)),
+                        rho_at<T>(mon, X0[pp].y(), X1[pp].y(), T(0)));
+  }
+  T gcv[4], rdv[4];
+#pragma unroll
+  for (int pp = 0; pp < 2; ++pp) {
+    const P2<T> rD = pmul(R[pp], DD[pp]);
+    P2<T> GC;
+    if (K.logrhs) {
+      GC = P2<T>::mk(Fm<T>::ln(rD.x()), Fm<T>::ln(rD.y()));
+      GC = padd(GC, K.NCL);
+    } else {
+      GC = P2<T>::mk(Fm<T>::pw(K.scale_root * rD.x(), K.inv_dim) - T(1) - K.c_lag,
+                     Fm<T>::pw(K.scale_root * rD.y(), K.inv_dim) - T(1) - K.c_lag);
+    }
+    const P2<T> vn = pfma(GC, K.DT2, P2<T>::mk(wC[2 * pp + 1], wC[2 * pp + 2]));
+    o.v[2 * pp] = vn.x();
+    o.v[2 * pp + 1] = vn.y();
+    gcv[2 * pp] = GC.x();
+    gcv[2 * pp + 1] = GC.y();
+    rdv[2 * pp] = rD.x();
+    rdv[2 * pp + 1] = rD.y();
+  }
+  const T rowu = rowdir ? T(0) : T(1);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const bool upd = uc.v[u] * rowu != T(0);
+    const T dv = u < 2 ? (u == 0 ? DD[0].x() : DD[0].y()) : (u == 2 ? DD[1].x() : DD[1].y());
+    A.gcmax = fmax(A.gcmax, upd ? gcv[u] : -big_val<T>());
+    A.gcmin = fmin(A.gcmin, upd ? gcv[u] : big_val<T>());
+    A.dmin = fmin(A.dmin, upd ? dv : big_val<T>());
+    const T g = upd ? gcv[u] : T(0);
+    const T rd = upd ? rdv[u] : T(0);
+    if (u & 1) {
+      A.gs2 = padd(A.gs2, P2<T>::mk(T(0), g));
+      A.th2 = pfma(P2<T>::mk(T(0), wc.v[u] * wyo), P2<T>::mk(T(0), rd), A.th2);
+    } else {
+      A.gs2 = padd(A.gs2, P2<T>::mk(g, T(0)));
+      A.th2 = pfma(P2<T>::mk(wc.v[u] * wyo, T(0)), P2<T>::mk(rd, T(0)), A.th2);
+    }
+    if (!upd) o.v[u] = T(0);
+  }
+  if (K.want_l2) {
+    Vec4<T> lc;
+    lc.lds(lcp);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool upd = uc.v[u] * rowu != T(0);
+      const T w = upd ? lc.v[u] * wly : T(0);
+      const T d = upd ? gcv[u] : T(0);
+      A.l2a = fma(w * d, d, A.l2a);
+      A.l2b = fma(w, d, A.l2b);
+      A.ws += w;
+    }
+  }
 }
 
 // ---------------------------------------------------------------- 2D sweep
@@ -662,23 +872,12 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
         }
       }
       __syncthreads();  // S2: band staged
-      const T c_lag = (T)H.ps.c_lag, dt = H.ph.dt;
-      const T scale_root = (T)(H.ph.vol / (T)H.ps.theta_prev);
-      const T inv2h0 = H.ph.inv2h[0], inv2h1 = H.ph.inv2h[1];
-      const T invh20 = H.ph.invh2[0], invh21 = H.ph.invh2[1], inv4 = H.ph.inv4hh[0];
-      const T lo0 = H.ph.lo[0], lo1 = H.ph.lo[1], h0 = H.ph.h[0], h1 = H.ph.h[1];
+      const T c_lag = (T)H.ps.c_lag;
+      const T h0 = H.ph.h[0], h1 = H.ph.h[1];
       const T hw0 = H.ph.hw[0], hw1 = H.ph.hw[1];
       const int N0 = H.ph.N[0], N1 = H.ph.N[1];
       const int clo0 = H.sd.clo[0], chi0 = H.sd.chi[0], clo1 = H.sd.clo[1], chi1 = H.sd.chi[1];
-      const bool want_l2 = H.ph.stop_norm == PMA_STOP_L2_INCREMENT;
       const bool run = phase == PH_RUN;
-      const bool logrhs = H.ph.rhs == PMA_RHS_LOG || !run;
-      const T inv_dim = T(1) / (T)H.ph.dim;
-      const int mkind = H.ph.mon.kind, nterms = H.ph.mon.nterms;
-      bool fast = (mkind == PMA_MON_SUM);
-      for (int q = 0; q < kMaxTerms; ++q)
-        if (q < nterms && H.ph.mon.t[q].type != PMA_TERM_BUMP && H.ph.mon.t[q].type != PMA_TERM_RING)
-          fast = false;
 
       // Per-column tables of the band (after the staged rows in shared
       // memory): theta weight of owned columns (0 elsewhere), 1 for updated
@@ -698,139 +897,17 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
       __syncthreads();
       // partial sums: theta, sum of (G - c) over updated nodes (a non-finite
       // value anywhere makes it non-finite), extrema of G - c, min det
-      P2<T> th2 = P2<T>::s(T(0)), gs2 = P2<T>::s(T(0));
-      T gcmax = -big_val<T>(), gcmin = big_val<T>();
-      const P2<T> NCL = P2<T>::s(-c_lag), DT2 = P2<T>::s(dt), M1 = P2<T>::s(T(-1));
-      const P2<T> M2 = P2<T>::s(T(-2)), ONE = P2<T>::s(T(1));
-      const P2<T> I2H0 = P2<T>::s(inv2h0), I2H1 = P2<T>::s(inv2h1);
-      const P2<T> IH20 = P2<T>::s(invh20), IH21 = P2<T>::s(invh21);
-      const P2<T> INV4 = P2<T>::s(inv4), NINV4 = P2<T>::s(-inv4);
+      const RunK<T> K = make_runk<T>(H.ph, H.ps, phase);
+      RunAcc<T> A = RunAcc<T>::zero();
       for (int q = tid; q < nruns; q += NT) {
         const int r = qdiv(q, rpr, inv_rpr), c0 = (q - r * rpr) * 4;
         const int j = j0 + r, gj = g01 + j;
-        const T* p = sv + (r + 1) * SWp + c0 + 4;
-        // 3 x 6 window: columns c0-1 .. c0+4 of rows j-1, j, j+1
-        T wS[6], wC[6], wN[6];
-        {
-          Vec4<T> m;
-          wS[0] = p[-SWp - 1];
-          m.lds(p - SWp);
-          wS[1] = m.v[0]; wS[2] = m.v[1]; wS[3] = m.v[2]; wS[4] = m.v[3];
-          wS[5] = p[-SWp + 4];
-          wC[0] = p[-1];
-          m.lds(p);
-          wC[1] = m.v[0]; wC[2] = m.v[1]; wC[3] = m.v[2]; wC[4] = m.v[3];
-          wC[5] = p[4];
-          wN[0] = p[SWp - 1];
-          m.lds(p + SWp);
-          wN[1] = m.v[0]; wN[2] = m.v[1]; wN[3] = m.v[2]; wN[4] = m.v[3];
-          wN[5] = p[SWp + 4];
-        }
-        Vec4<T> wc, uc;
-        wc.lds(wcol + c0);
-        uc.lds(ucol + c0);
         const bool rowdir = (j == dly || j == dhy);
         const T wyo = (j >= clo1 && j <= chi1) ? ((gj == 0 || gj == N1 - 1) ? hw1 : h1) : T(0);
-        const T xi1 = fma((T)gj, h1, lo1);
-        const int gi0 = g00 + i0 + c0;
-        const P2<T> dA = psub(P2<T>::mk(wN[0], wN[1]), P2<T>::mk(wS[0], wS[1]));
-        const P2<T> dB = psub(P2<T>::mk(wN[2], wN[3]), P2<T>::mk(wS[2], wS[3]));
-        const P2<T> dC = psub(P2<T>::mk(wN[4], wN[5]), P2<T>::mk(wS[4], wS[5]));
-        P2<T> X0[2], X1[2], DD[2], R[2];
-#pragma unroll
-        for (int pp = 0; pp < 2; ++pp) {
-          const P2<T> C = P2<T>::mk(wC[2 * pp + 1], wC[2 * pp + 2]);
-          const P2<T> E = P2<T>::mk(wC[2 * pp + 2], wC[2 * pp + 3]);
-          const P2<T> Wv = P2<T>::mk(wC[2 * pp], wC[2 * pp + 1]);
-          const P2<T> Nn = P2<T>::mk(wN[2 * pp + 1], wN[2 * pp + 2]);
-          const P2<T> Ss = P2<T>::mk(wS[2 * pp + 1], wS[2 * pp + 2]);
-          const P2<T> XI0 = P2<T>::mk(fma((T)(gi0 + 2 * pp), h0, lo0),
-                                      fma((T)(gi0 + 2 * pp + 1), h0, lo0));
-          X0[pp] = pfma(psub(E, Wv), I2H0, XI0);
-          X1[pp] = pfma(psub(Nn, Ss), I2H1, P2<T>::s(xi1));
-          const P2<T> hxx = pfma(pfma(C, M2, padd(E, Wv)), IH20, ONE);
-          const P2<T> hyy = pfma(pfma(C, M2, padd(Nn, Ss)), IH21, ONE);
-          const P2<T> df = pp == 0 ? psub(dB, dA) : psub(dC, dB);
-          DD[pp] = pfma(pmul(df, INV4), pmul(df, NINV4), pmul(hxx, hyy));
-        }
-        if (fast) {
-          // sum of Gaussian bumps / rings, two nodes per operation
-#pragma unroll
-          for (int pp = 0; pp < 2; ++pp) R[pp] = P2<T>::s(H.ph.mon.base);
-          for (int k = 0; k < nterms; ++k) {
-            const auto& tm = H.ph.mon.t[k];
-            const P2<T> CX = P2<T>::s(tm.c[0]), CY = P2<T>::s(tm.c[1]), R2 = P2<T>::s(tm.r2);
-            const P2<T> NWd = P2<T>::s(-tm.width), AMP = P2<T>::s(tm.amp);
-            const bool ring = tm.type == PMA_TERM_RING;
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-              const P2<T> d0 = psub(X0[pp], CX), d1 = psub(X1[pp], CY);
-              const P2<T> qq = pfma(d0, d0, pmul(d1, d1));
-              const P2<T> s2 = psub(qq, R2);
-              const P2<T> uu = ring ? pmul(s2, s2) : qq;
-              R[pp] = pfma(AMP, pexw<T>(pmul(uu, NWd)), R[pp]);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int pp = 0; pp < 2; ++pp)
-            R[pp] = P2<T>::mk(rho_at<T>(H.ph.mon, X0[pp].x(), X1[pp].x(), T(0)),
-                              rho_at<T>(H.ph.mon, X0[pp].y(), X1[pp].y(), T(0)));
-        }
+        const T wly = (j == 0 || j == n1 - 1) ? hw1 : h1;
         Vec4<T> o;
-        T gcv[4], rdv[4];
-#pragma unroll
-        for (int pp = 0; pp < 2; ++pp) {
-          const P2<T> rD = pmul(R[pp], DD[pp]);
-          P2<T> GC;
-          if (logrhs) {
-            GC = P2<T>::mk(Fm<T>::ln(rD.x()), Fm<T>::ln(rD.y()));
-            GC = padd(GC, NCL);
-          } else {
-            GC = P2<T>::mk(Fm<T>::pw(scale_root * rD.x(), inv_dim) - T(1) - c_lag,
-                           Fm<T>::pw(scale_root * rD.y(), inv_dim) - T(1) - c_lag);
-          }
-          const P2<T> vn = pfma(GC, DT2, P2<T>::mk(wC[2 * pp + 1], wC[2 * pp + 2]));
-          o.v[2 * pp] = vn.x();
-          o.v[2 * pp + 1] = vn.y();
-          gcv[2 * pp] = GC.x();
-          gcv[2 * pp + 1] = GC.y();
-          rdv[2 * pp] = rD.x();
-          rdv[2 * pp + 1] = rD.y();
-        }
-        const T rowu = rowdir ? T(0) : T(1);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const bool upd = uc.v[u] * rowu != T(0);
-          const T dv = u < 2 ? (u == 0 ? DD[0].x() : DD[0].y()) : (u == 2 ? DD[1].x() : DD[1].y());
-          gcmax = fmax(gcmax, upd ? gcv[u] : -big_val<T>());
-          gcmin = fmin(gcmin, upd ? gcv[u] : big_val<T>());
-          acc.dmin = fmin(acc.dmin, upd ? dv : big_val<T>());
-          const T g = upd ? gcv[u] : T(0);
-          const T rd = upd ? rdv[u] : T(0);
-          if (u & 1) {
-            gs2 = padd(gs2, P2<T>::mk(T(0), g));
-            th2 = pfma(P2<T>::mk(T(0), wc.v[u] * wyo), P2<T>::mk(T(0), rd), th2);
-          } else {
-            gs2 = padd(gs2, P2<T>::mk(g, T(0)));
-            th2 = pfma(P2<T>::mk(wc.v[u] * wyo, T(0)), P2<T>::mk(rd, T(0)), th2);
-          }
-          if (!upd) o.v[u] = T(0);
-        }
-        if (want_l2) {
-          Vec4<T> lc;
-          lc.lds(lcol + c0);
-          const T wly = (j == 0 || j == n1 - 1) ? hw1 : h1;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const bool upd = uc.v[u] * rowu != T(0);
-            const T w = upd ? lc.v[u] * wly : T(0);
-            const T d = upd ? gcv[u] : T(0);
-            l2a = fma(w * d, d, l2a);
-            l2b = fma(w, d, l2b);
-            ws += w;
-          }
-        }
+        stencil_run4<T>(K, H.ph.mon, sv + (r + 1) * SWp + c0 + 4, SWp, wcol + c0, ucol + c0,
+                        lcol + c0, rowdir, wyo, wly, fma((T)gj, K.h1, K.lo1), g00 + i0 + c0, o, A);
         if (run) {
           if (rowdir || (i0 + c0 <= dlx) || (i0 + c0 + 3 >= dhx && dhx >= 0)) {
 #pragma unroll
@@ -843,6 +920,12 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
           o.stg(dst + j * pitch + i0 + c0);
         }
       }
+      const P2<T> th2 = A.th2, gs2 = A.gs2;
+      const T gcmax = A.gcmax, gcmin = A.gcmin;
+      acc.dmin = A.dmin;
+      l2a = A.l2a;
+      l2b = A.l2b;
+      ws = A.ws;
       th = th2.x() + th2.y();
       if (gcmax > -big_val<T>()) acc.gmax = gcmax + c_lag;
       if (gcmin < big_val<T>()) acc.gmin = gcmin + c_lag;
@@ -894,6 +977,388 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
     }
   }
   if (tid == 0) queue_exit(a);
+}
+
+// ---------------------------------------------------------------- resident 2D
+// k_res2d: one CTA per subdomain, the whole subdomain in shared memory for
+// up to `iters` steps of the parallel DD method (Sect. 3), thread-block
+// clusters holding all subdomains of a problem.  Per step:
+//   1. after the cluster barrier, warp 0 folds the problem's per-subdomain
+//      records of the previous step (read from the other CTAs' shared
+//      memory, fixed order) into theta, c^n, the residual and the stop test,
+//      exactly as the batched finish does;
+//   2. transmission nodes (Eq. transmission_condition3): the value copied one
+//      step earlier gets the offset correction, and the owner's current value
+//      is copied (distributed shared memory) into the next buffer;
+//   3. every run of 4 nodes is updated from the current buffer into the next
+//      one (same arithmetic as the band kernel), mirror ghosts of physical
+//      faces (Eq. nbd) are written alongside;
+//   4. the CTA's record goes to its shared memory; cluster barrier.
+// Dynamic shared memory: buffer 0 and 1 (`cap` elements each; buffer b holds
+// v[b], subdomain row j at (j+1)*SWp, node column i at i+4, one halo row and
+// column on every side), then the column tables and the transmission list
+// (int2: local position, owner rank << 20 | position in the owner's buffer).
+struct ResDecide {
+  double vol, dt, tol;
+  long long max_steps;
+  int nsub, stop_norm, stop_rule, check_every, rhs, normalize;
+};
+
+// Step 1 for one problem (warp 0 of each of its CTAs; identical inputs and
+// order in every CTA, so all of them take the same decision).
+__device__ __forceinline__ void res_decide(ProbState& ps, const ResDecide& dk, const Partial* recs,
+                                           int rank0, int lane) {
+  const int ph0 = ps.phase;
+  const double c_lag = ps.c_lag;
+  __syncwarp();
+  const bool mine = lane < dk.nsub;
+  double th = 0.0, gx = -DBL_MAX, gn = DBL_MAX, dm = DBL_MAX, A = 0.0, B = 0.0, Wt = 0.0;
+  int nf = 0;
+  if (mine) {
+    const unsigned int ra = dsmem_map(recs, (unsigned int)(rank0 + lane));
+    th = dsmem_ld(ra + (unsigned int)offsetof(Partial, theta), 0.0);
+    A = dsmem_ld(ra + (unsigned int)offsetof(Partial, l2a), 0.0);
+    B = dsmem_ld(ra + (unsigned int)offsetof(Partial, l2b), 0.0);
+    Wt = dsmem_ld(ra + (unsigned int)offsetof(Partial, wsum), 0.0);
+    gx = dsmem_ld(ra + (unsigned int)offsetof(Partial, gmax), 0.0);
+    gn = dsmem_ld(ra + (unsigned int)offsetof(Partial, gmin), 0.0);
+    dm = dsmem_ld(ra + (unsigned int)offsetof(Partial, dmin), 0.0);
+    nf = dsmem_ld(ra + (unsigned int)offsetof(Partial, nonfinite), 0);
+  }
+  const double gxs = gx, gns = gn;
+  th = warp_dsum(th);
+  gx = warp_max(gx);
+  gn = warp_min(gn);
+  dm = warp_min(dm);
+  nf = warp_isum(nf);
+  const double theta = th;
+  double c_n = 0.0;
+  if (dk.rhs == PMA_RHS_LOG && dk.normalize == PMA_NORM_GLOBAL_THETA) c_n = log(theta / dk.vol);
+  const bool tangled = nf > 0 || !(dm > 0.0) || !isfinite(theta);
+  if (ph0 == PH_INIT_THETA) {
+    if (lane == 0) advance_init(&ps, theta, c_n, dm, tangled, dk.max_steps);
+    __syncwarp();
+    return;
+  }
+  const bool any = (dk.stop_rule == PMA_RULE_ANY);
+  double r;
+  if (dk.stop_norm == PMA_STOP_MAX_UT && !any) {
+    r = fmax(gx - c_n, c_n - gn);
+  } else {
+    double r_s;
+    if (dk.stop_norm == PMA_STOP_MAX_UT) {
+      r_s = fmax(gxs - c_n, c_n - gns);
+    } else {
+      const double delta = c_n - c_lag;
+      const double q = A - 2.0 * delta * B + delta * delta * Wt;
+      r_s = dk.dt * sqrt(q > 0.0 ? q : 0.0);
+    }
+    if (!mine) r_s = any ? INFINITY : 0.0;
+    r = any ? warp_min(r_s) : warp_max(r_s);
+  }
+  if (lane == 0)
+    advance_run(&ps, theta, c_n, dm, tangled, r, dk.dt, dk.check_every, dk.tol, dk.max_steps);
+  __syncwarp();
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_res2d(ResArgs a) {
+  constexpr int NW = NT / 32;
+  constexpr int VW = 16 / (int)sizeof(T);
+  extern __shared__ __align__(16) unsigned char res_smem[];
+  T* const buf = (T*)res_smem;
+  __shared__ __align__(16) SubDesc sd;
+  __shared__ __align__(16) ProbHot<T> ph;
+  __shared__ __align__(16) ProbState ps;
+  __shared__ ResDecide dk;
+  __shared__ __align__(16) Partial rec[2];
+  __shared__ int act[2];
+  __shared__ int rank_cap[kResClusterMax];
+  __shared__ int s_ndir, s_exit;
+  __shared__ T red_t[4 * NW];
+  __shared__ T red_f[3 * NW];
+  __shared__ int red_i[NW];
+
+  const int tid = threadIdx.x, lane = tid & 31;
+  const ResCta me = a.ctas[blockIdx.x];
+  const bool has = me.sub >= 0;
+  const int csize = (int)cluster_size();
+  const ProbHot<T>* hot = (const ProbHot<T>*)(sizeof(T) == 4 ? (const void*)a.hotf
+                                                               : (const void*)a.hotd);
+  const int prob = has ? __ldg(&a.subs[me.sub].prob) : 0;
+  if (has) {
+    coop_copy<NT>(&sd, a.subs + me.sub, (int)sizeof(SubDesc), 0);
+    coop_copy<NT>(&ph, hot + prob, (int)sizeof(ProbHot<T>), 0);
+    coop_copy<NT>(&ps, a.st + prob, (int)sizeof(ProbState), 0);
+    if (tid == 0) {
+      const ProbDesc& pd = a.probs[prob];
+      dk.vol = pd.vol;
+      dk.dt = pd.dt;
+      dk.tol = pd.tol;
+      dk.max_steps = pd.max_steps;
+      dk.nsub = pd.nsub;
+      dk.stop_norm = pd.stop_norm;
+      dk.stop_rule = pd.stop_rule;
+      dk.check_every = pd.check_every;
+      dk.rhs = pd.rhs;
+      dk.normalize = pd.normalize;
+    }
+    // buffer capacity of every CTA of the problem (owners of transmission
+    // values are read at buffer parity * capacity + position)
+    const int nsub = __ldg(&a.probs[prob].nsub), base = __ldg(&a.probs[prob].sub_base);
+    if (tid < nsub)
+      rank_cap[me.rank0 + tid] =
+          res_cap_elems(__ldg(&a.subs[base + tid].n[0]), __ldg(&a.subs[base + tid].n[1]));
+  }
+  if (tid == 0) {
+    act[0] = act[1] = 0;
+    s_ndir = 0;
+    s_exit = 0;
+  }
+  __syncthreads();
+
+  int n0 = 4, n1 = 4, cr = 4, SWp = 12, g00 = 0, g01 = 0, cap = 0;
+  int clo1 = 0, chi1 = 0, N1 = 1, dlx = -1, dhx = -1, dly = -1, dhy = -1;
+  bool plx = true, phx = true, ply = true, phy = true, loaded = false;
+  T h1 = 0, hw1 = 0;
+  T *wcol = buf, *ucol = buf, *lcol = buf, *dorig = buf;
+  int2* dlist = (int2*)buf;
+  if (has) {
+    n0 = sd.n[0];
+    n1 = sd.n[1];
+    cr = (n0 + 3) & ~3;
+    SWp = cr + 8;
+    cap = res_cap_elems(n0, n1);
+    g00 = sd.g0[0];
+    g01 = sd.g0[1];
+    const int faces = sd.faces;
+    plx = faces & 1;
+    phx = faces & 2;
+    ply = faces & 4;
+    phy = faces & 8;
+    dlx = plx ? -1 : 0;
+    dhx = phx ? -1 : n0 - 1;
+    dly = ply ? -1 : 0;
+    dhy = phy ? -1 : n1 - 1;
+    clo1 = sd.clo[1];
+    chi1 = sd.chi[1];
+    N1 = ph.N[1];
+    h1 = ph.h[1];
+    hw1 = ph.hw[1];
+    wcol = buf + 2 * cap;
+    ucol = wcol + cr;
+    lcol = ucol + cr;
+    dlist = (int2*)(lcol + cr);
+    dorig = (T*)(dlist + 2 * (n0 + n1) + 8);
+    // column tables: theta weight of owned columns, 1 for updated columns,
+    // local trapezoid weight
+    {
+      const int clo0 = sd.clo[0], chi0 = sd.chi[0], N0 = ph.N[0];
+      const T h0 = ph.h[0], hw0 = ph.hw[0];
+      for (int c = tid; c < cr; c += NT) {
+        const int gi = g00 + c;
+        const bool valid = c < n0;
+        wcol[c] = (valid && c >= clo0 && c <= chi0) ? ((gi == 0 || gi == N0 - 1) ? hw0 : h0) : T(0);
+        ucol[c] = (valid && c != dlx && c != dhx) ? T(1) : T(0);
+        lcol[c] = (c == 0 || c == n0 - 1) ? hw0 : h0;
+      }
+    }
+    // transmission nodes on the subdomain's ring, with their owners (the
+    // neighbouring block whose core holds the node) and the mirror images
+    // that the Neumann faces give them
+    const int ring = 2 * n0 + 2 * (n1 - 2);
+    for (int e = tid; e < ring; e += NT) {
+      int i, j;
+      if (e < n0) {
+        i = e;
+        j = 0;
+      } else if (e < 2 * n0) {
+        i = e - n0;
+        j = n1 - 1;
+      } else {
+        const int k = e - 2 * n0;
+        i = (k & 1) ? n0 - 1 : 0;
+        j = 1 + (k >> 1);
+      }
+      if (!(i == dlx || i == dhx || j == dly || j == dhy)) continue;
+      const int kx = sd.k[0] + (i < sd.clo[0] ? -1 : (i > sd.chi[0] ? 1 : 0));
+      const int ky = sd.k[1] + (j < sd.clo[1] ? -1 : (j > sd.chi[1] ? 1 : 0));
+      const int oidx = ky * ph.parts[0] + kx;
+      const SubDesc* od = a.subs + ph.sub_base + oidx;
+      const int ox = g00 + i - __ldg(&od->g0[0]);
+      const int oy = g01 + j - __ldg(&od->g0[1]);
+      const int oswp = ((__ldg(&od->n[0]) + 3) & ~3) + 8;
+      const int src = ((me.rank0 + oidx) << 20) | ((oy + 1) * oswp + ox + 4);
+      const int xm = (plx && i == 1) ? -1 : ((phx && i == n0 - 2) ? n0 : -2);
+      const int ym = (ply && j == 1) ? -1 : ((phy && j == n1 - 2) ? n1 : -2);
+      const int nx = xm != -2 ? 2 : 1, ny = ym != -2 ? 2 : 1;
+      const int slot = atomicAdd(&s_ndir, nx * ny);
+      int q = 0;
+      for (int b = 0; b < ny; ++b)
+        for (int c = 0; c < nx; ++c) {
+          const int jj = b ? ym : j, ii = c ? xm : i;
+          dlist[slot + q++] = make_int2((jj + 1) * SWp + ii + 4, src);
+        }
+    }
+    // state v[parity] (or v^0) with mirror / clamp halos into both buffers
+    const int phase0 = ps.phase;
+    loaded = phase0 != PH_DONE;
+    if (loaded) {
+      const int par = ps.parity;
+      const T* g = (const T*)sd.v[par];
+      const long long pitch = sd.pitch;
+      const double* psi0 = a.probs[prob].psi0;
+      const int Nx = ph.N[0];
+      for (int e = tid; e < (n1 + 2) * SWp; e += NT) {
+        const int r = e / SWp, c = e - r * SWp;
+        const int i = c - 4, j = r - 1;
+        T val = T(0);
+        if (i >= -1 && i <= n0) {
+          const int ii = reflect_clamp(i, n0, plx, phx), jj = reflect_clamp(j, n1, ply, phy);
+          if (phase0 == PH_INIT_V) {
+            if (psi0) {
+              const int gi = g00 + ii, gj = g01 + jj;
+              const double xi = (double)ph.lo[0] + (double)gi * ph.hd[0];
+              const double et = (double)ph.lo[1] + (double)gj * ph.hd[1];
+              val = (T)(psi0[(long long)gj * Nx + gi] - 0.5 * (xi * xi + et * et));
+            }
+          } else {
+            val = __ldcg(g + jj * pitch + ii);
+          }
+        }
+        buf[par * cap + e] = val;
+        buf[(par ^ 1) * cap + e] = val;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && has && ps.phase == PH_INIT_V) ps.phase = PH_INIT_THETA;
+  // every CTA of the cluster has loaded its state before any other CTA reads
+  // it through shared::cluster (the first step's transmission values)
+  cluster_arrive();
+  cluster_wait();
+
+  const int rpr = cr >> 2;
+  const int nruns = n1 * rpr;
+  const float inv_rpr = 1.0f / (float)rpr;
+  bool computed = false;
+  int dpar = -1;  // buffer whose transmission values carry the last correction
+  for (int it = 0;; ++it) {
+    if (it > 0) {
+      cluster_wait();
+      if (tid < 32) {
+        const int slot = (it - 1) & 1;
+        int f = 0;
+        if (lane < csize) f = dsmem_ld(dsmem_map(&act[slot], (unsigned int)lane), 0);
+        const bool any = __any_sync(0xffffffffu, f != 0);
+        if (computed) res_decide(ps, dk, &rec[slot], me.rank0, lane);
+        if (lane == 0) s_exit = (!any || it >= a.iters) ? 1 : 0;
+      }
+      __syncthreads();
+      if (s_exit) break;
+    } else if (a.iters <= 0) {
+      break;
+    }
+    const int phase = has ? ps.phase : PH_DONE;
+    computed = (phase == PH_INIT_THETA || phase == PH_RUN);
+    if (computed) {
+      const int par = ps.parity;
+      T* const cur = buf + par * cap;
+      T* const nxt = buf + (par ^ 1) * cap;
+      const bool run = phase == PH_RUN;
+      if (run) {
+        const T corr = (T)ps.corr;
+        const int nd = s_ndir;
+        for (int e = tid; e < nd; e += NT) {
+          const int2 d = dlist[e];
+          const unsigned int rank = (unsigned int)d.y >> 20;
+          const int off = par * rank_cap[rank] + (d.y & 0xfffff);
+          const T v0 = cur[d.x];
+          dorig[e] = v0;
+          cur[d.x] = v0 + corr;
+          nxt[d.x] = dsmem_ld(dsmem_map(buf + off, rank), T(0));
+        }
+        dpar = par;
+        __syncthreads();
+      }
+      const RunK<T> K = make_runk<T>(ph, ps, phase);
+      RunAcc<T> A = RunAcc<T>::zero();
+      for (int q = tid; q < nruns; q += NT) {
+        const int r = qdiv(q, rpr, inv_rpr), c0 = (q - r * rpr) * 4;
+        const int j = r, gj = g01 + j;
+        const bool rowdir = (j == dly || j == dhy);
+        const T wyo = (j >= clo1 && j <= chi1) ? ((gj == 0 || gj == N1 - 1) ? hw1 : h1) : T(0);
+        const T wly = (j == 0 || j == n1 - 1) ? hw1 : h1;
+        Vec4<T> o;
+        stencil_run4<T>(K, ph.mon, cur + (r + 1) * SWp + c0 + 4, SWp, wcol + c0, ucol + c0,
+                        lcol + c0, rowdir, wyo, wly, fma((T)gj, K.h1, K.lo1), g00 + c0, o, A);
+        if (run && !rowdir) {
+          T* const d = nxt + (r + 1) * SWp + c0 + 4;
+          const int jm = (ply && j == 1) ? -1 : ((phy && j == n1 - 2) ? n1 : -2);
+          T* const dmr = nxt + (jm + 1) * SWp + c0 + 4;
+          if (c0 != 0 && c0 + 3 < n0 - 2) {
+            o.sts(d);
+            if (jm != -2) o.sts(dmr);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int c = c0 + u;
+              if (c < n0 && c != dlx && c != dhx) {
+                d[u] = o.v[u];
+                if (jm != -2) dmr[u] = o.v[u];
+                const int cm = (plx && c == 1) ? -1 : ((phx && c == n0 - 2) ? n0 : -2);
+                if (cm != -2) {
+                  d[cm - c0] = o.v[u];
+                  if (jm != -2) dmr[cm - c0] = o.v[u];
+                }
+              }
+            }
+          }
+        }
+      }
+      T th = A.th2.x() + A.th2.y();
+      Acc<T> acc{-big_val<T>(), big_val<T>(), A.dmin, 0};
+      if (A.gcmax > -big_val<T>()) acc.gmax = A.gcmax + K.c_lag;
+      if (A.gcmin < big_val<T>()) acc.gmin = A.gcmin + K.c_lag;
+      if (!isfinite(A.gs2.x() + A.gs2.y())) acc.nf += 1;
+      tile_reduce<T, NT>(th, A.l2a, A.l2b, A.ws, acc, &rec[it & 1], me.sub, red_t, red_f, red_i);
+      if (tid == 0) act[it & 1] = 1;
+    } else {
+      if (tid == 0) act[it & 1] = 0;
+    }
+    cluster_arrive();
+  }
+  // no CTA leaves while another may still read its shared memory
+  cluster_arrive();
+  cluster_wait();
+  if (has && loaded) {
+    const int par = ps.parity;
+    T* const cur = buf + par * cap;
+    if (dpar == par) {
+      // a step that tangled keeps the state it read: its transmission values
+      // go back without the correction (still pending in the state)
+      const int nd = s_ndir;
+      for (int e = tid; e < nd; e += NT) cur[dlist[e].x] = dorig[e];
+      __syncthreads();
+    }
+    T* g = (T*)sd.v[par];
+    const int pitch = sd.pitch;
+    const int cpr = pitch / VW;
+    for (int e = tid; e < n1 * cpr; e += NT) {
+      const int r = e / cpr, k = e - r * cpr;
+      Vec4<T> o;
+      o.lds(cur + (r + 1) * SWp + 4 + k * VW);
+      if (VW == 4) {
+        o.stg(g + (long long)r * pitch + k * VW);
+      } else {
+        st_global(g + (long long)r * pitch + k * VW, o.v[0]);
+        st_global(g + (long long)r * pitch + k * VW + 1, o.v[1]);
+      }
+    }
+    if ((int)cluster_rank() == me.rank0)
+      for (int i = tid; i < (int)(sizeof(ProbState) / 16); i += NT)
+        ((int4*)(a.st + prob))[i] = ((const int4*)&ps)[i];
+  }
 }
 
 // ---------------------------------------------------------------- 3D sweep
@@ -1442,6 +1907,88 @@ int sweep_max_blocks_per_sm(int cls, int tile_id) {
   return nb > 0 ? nb : 1;
 }
 
+// ---------------------------------------------------------------- resident dispatch
+// Classes of the resident path: dynamic shared memory per CTA and threads.
+// FP64 uses at most 512 threads (register budget of the FP64 stencil).
+static const int k_res[kResClasses][2] = {
+    {24 * 1024, 128}, {56 * 1024, 256}, {112 * 1024, 512}, {220 * 1024, 1024}};
+
+static int res_threads(bool fp64, int id) {
+  const int nt = k_res[id][1];
+  return (fp64 && nt > 512) ? 512 : nt;
+}
+
+ResClass res_class(int id, bool fp64) { return ResClass{k_res[id][0], res_threads(fp64, id)}; }
+
+static const void* res_fn(bool fp64, int id) {
+  const int nt = k_res[id][1];
+  if (fp64) {
+    switch (nt) {
+      case 128: return (const void*)k_res2d<double, 128>;
+      case 256: return (const void*)k_res2d<double, 256>;
+      default: return (const void*)k_res2d<double, 512>;
+    }
+  }
+  switch (nt) {
+    case 128: return (const void*)k_res2d<float, 128>;
+    case 256: return (const void*)k_res2d<float, 256>;
+    case 512: return (const void*)k_res2d<float, 512>;
+    default: return (const void*)k_res2d<float, 1024>;
+  }
+}
+
+// Every resident kernel may take the largest class budget (a launch uses
+// the largest need among its CTAs).
+cudaError_t prepare_res_kernels() {
+  for (int f = 0; f < 2; ++f)
+    for (int id = 0; id < kResClasses; ++id) {
+      const void* fn = res_fn(f == 1, id);
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           k_res[kResClasses - 1][0]);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+static void res_config(bool fp64, int id, int nclusters, int csize, int smem_bytes,
+                       cudaStream_t s, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at) {
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = dim3((unsigned int)(nclusters * csize), 1, 1);
+  cfg->blockDim = dim3((unsigned int)res_threads(fp64, id), 1, 1);
+  cfg->dynamicSmemBytes = (size_t)smem_bytes;
+  cfg->stream = s;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned int)csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg->attrs = at;
+  cfg->numAttrs = 1;
+}
+
+int res_max_clusters(bool fp64, int id, int csize, int smem_bytes) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute at[1];
+  res_config(fp64, id, 1, csize, smem_bytes, nullptr, &cfg, at);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, res_fn(fp64, id), &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_res2d(bool fp64, int id, const ResArgs& a, int nclusters, int csize,
+                         int smem_bytes, cudaStream_t s) {
+  if (nclusters <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute at[1];
+  res_config(fp64, id, nclusters, csize, smem_bytes, s, &cfg, at);
+  void* args[] = {(void*)&a};
+  return cudaLaunchKernelExC(&cfg, res_fn(fp64, id), args);
+}
+
 // ---------------------------------------------------------------- combine
 // Owner-takes combination: global node g takes x = xi + grad_h v of the
 // subdomain whose core holds it (mirror ghost on faces of Omega_c, i.e.
@@ -1503,15 +2050,31 @@ __device__ void combine_node(const CombineJob& J, long long g, const SubDesc* su
   }
 }
 
-__global__ void k_combine(const CombineJob* jobs, int njobs, const SubDesc* subs,
-                          const ProbDesc* probs, const ProbState* st) {
-  const CombineJob J = jobs[blockIdx.y];
+__global__ void __launch_bounds__(256) k_combine(const CombineJob* jobs, int njobs,
+                                                 const SubDesc* subs, const ProbDesc* probs,
+                                                 const ProbState* st) {
+  __shared__ int s_job;
+  if (threadIdx.x == 0) {
+    // last job whose first block is <= this block
+    int lo = 0, hi = njobs - 1;
+    const long long b = blockIdx.x;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].block_begin <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    s_job = lo;
+  }
+  __syncthreads();
+  const CombineJob J = jobs[s_job];
   const ProbDesc& pd = probs[J.prob];
   const ProbState& ps = st[J.prob];
   const long long N = (long long)pd.N[0] * pd.N[1] * pd.N[2];
   const bool f64 = (pd.cls == CLS_2D_F64 || pd.cls == CLS_3D_F64);
-  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N;
-       g += (long long)gridDim.x * blockDim.x) {
+  const long long g0 = ((long long)blockIdx.x - J.block_begin) * kCombineNodes;
+  for (int k = threadIdx.x; k < kCombineNodes; k += blockDim.x) {
+    const long long g = g0 + k;
+    if (g >= N) break;
     if (f64)
       combine_node<double>(J, g, subs, pd, ps);
     else
@@ -1519,14 +2082,11 @@ __global__ void k_combine(const CombineJob* jobs, int njobs, const SubDesc* subs
   }
 }
 
-cudaError_t launch_combine(const CombineJob* jobs_dev, int njobs, long long max_nodes,
+cudaError_t launch_combine(const CombineJob* jobs_dev, int njobs, long long total_blocks,
                            const SubDesc* subs, const ProbDesc* probs, const ProbState* st,
                            cudaStream_t s) {
-  if (njobs <= 0) return cudaSuccess;
-  long long bx = (max_nodes + 255) / 256;
-  if (bx > 4096) bx = 4096;
-  if (bx < 1) bx = 1;
-  k_combine<<<dim3((unsigned)bx, (unsigned)njobs), 256, 0, s>>>(jobs_dev, njobs, subs, probs, st);
+  if (njobs <= 0 || total_blocks <= 0) return cudaSuccess;
+  k_combine<<<(unsigned)total_blocks, 256, 0, s>>>(jobs_dev, njobs, subs, probs, st);
   return cudaGetLastError();
 }
 

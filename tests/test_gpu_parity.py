@@ -61,14 +61,15 @@ def test_config1_uncapped_converges_at_same_step():
     assert info.status == pma.PMA_OK and info.steps == ref.steps == 2857
 
 
+@pytest.mark.parametrize("resident", [0, 4])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("n,parts,o", [((45, 37), (3, 2), 5), ((70, 33), (1, 3), 4),
                                        ((21, 64), (2, 1), 2), ((97, 65), (4, 3), 8)])
-def test_dd_2d_ragged(prec, n, parts, o):
+def test_dd_2d_ragged(prec, n, parts, o, resident):
     prob = W.Problem(dim=2, n=(n[0], n[1], 1), monitor=W.ring_monitor(), parts=(parts[0], parts[1], 1),
                      overlap=o, dt=W.dt_for((n[0], n[1], 1), 2), tol=0.0, max_steps=150,
                      precision=prec)
-    _check(prob)
+    _check(prob, resident=resident, window_steps=40)
 
 
 @pytest.mark.parametrize("mon", ["sine", "bumps", "product", "burgers"])
@@ -163,16 +164,105 @@ def test_monitor_kinds_3d(mon):
 def test_launch_modes_are_bitwise_identical():
     prob = W.Problem(dim=2, n=(50, 44, 1), monitor=W.ring_monitor(), parts=(3, 2, 1), overlap=6,
                      dt=W.dt_for((50, 44, 1), 2), tol=0.0, max_steps=77, precision="fp32")
-    a = pma.solve(prob, window_steps=32)[0]
-    b = pma.solve(prob, window_steps=5, use_graphs=0)[0]
+    a = pma.solve(prob, window_steps=32, resident=0)[0]
+    b = pma.solve(prob, window_steps=5, use_graphs=0, resident=0)[0]
     c = pma.solve(prob, launch_mode=pma.PMA_LAUNCH_PER_SUBDOMAIN, window_steps=16)[0]
     assert np.array_equal(a, b) and np.array_equal(a, c)
-    # another tile shape changes the summation order of theta (a uniform
-    # offset of v), so positions agree to rounding, not bitwise
+    # the resident path does not depend on the window either
+    r1 = pma.solve(prob, window_steps=32, resident=4)[0]
+    r2 = pma.solve(prob, window_steps=3, resident=4)[0]
+    assert np.array_equal(r1, r2)
+    # another tile shape, or the resident path, changes the summation order
+    # of theta (a uniform offset of v), so positions agree to rounding
     ref = oracle.solve(prob)
+    assert np.abs(r1 - a).max() < 1e-6 and np.abs(r1 - ref.x).max() < TOL32
     for t in range(4):
-        d = pma.solve(prob, tile_2d=t)[0]
+        d = pma.solve(prob, tile_2d=t, resident=0)[0]
         assert np.abs(d - a).max() < 1e-6 and np.abs(d - ref.x).max() < TOL32
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("variant", ["ragged", "l2_any", "tangle", "warm"])
+def test_band_and_resident_paths_both_match_the_oracle(prec, variant):
+    """The 2D band kernels (resident path off) and the cluster-resident path
+    against the oracle on the same problem; the resident path really ran."""
+    if variant == "ragged":
+        prob = W.Problem(dim=2, n=(61, 47, 1), monitor=W.sine_monitor(), parts=(4, 3, 1),
+                         overlap=5, dt=W.dt_for((61, 47, 1), 2), tol=0.0, max_steps=140,
+                         precision=prec)
+    elif variant == "l2_any":
+        # the per-subdomain L2 increments combined by ANY (no stop: the
+        # residual itself is compared)
+        prob = W.Problem(dim=2, n=(40, 52, 1), monitor=W.ring_monitor(), parts=(2, 3, 1),
+                         overlap=6, dt=W.dt_for((40, 52, 1), 2), tol=0.0, max_steps=150,
+                         precision=prec, stop_norm="l2_increment", stop_rule="any")
+    elif variant == "tangle":
+        prob = W.small_case(2, 25, parts=(2, 2, 1), overlap=4, steps=400, precision=prec).replace(
+            dt=W.dt_for((25, 25, 1), 2, cfl=4.0))
+    else:
+        prob = W.Problem(dim=2, n=(37, 41, 1), monitor=W.ring_monitor(), parts=(2, 2, 1),
+                         overlap=4, dt=W.dt_for((37, 41, 1), 2), tol=0.0, max_steps=60,
+                         precision=prec)
+    psi0 = None
+    if variant == "warm":
+        psi0 = oracle.solve(prob.replace(max_steps=40, precision="fp64")).psi
+    ref = oracle.solve(prob, psi0)
+    tol = TOL64 if prec == "fp64" else TOL32
+    if variant == "tangle":
+        tol = max(tol, 1e-9)
+    for resident in (0, 4):
+        with pma.Context(0, resident=resident, window_steps=16) as ctx:
+            rid = ctx.submit(prob, psi0)
+            ctx.run()
+            x, _, info = ctx.mesh(prob, rid)
+            _, stats = pma.pma_get_stats(ctx.h)
+        assert (stats.res_launches > 0) == bool(resident)
+        assert info.steps == ref.steps and pma.STATUS_NAMES[info.status] == ref.status
+        assert np.abs(x - ref.x).max() / _size(prob) <= tol, (resident, np.abs(x - ref.x).max())
+        if variant == "l2_any":
+            rel = 1e-8 if prec == "fp64" else 1e-3
+            assert abs(info.residual - ref.residual) <= rel * ref.residual
+
+
+def test_resident_and_band_agree_on_an_uneven_batch():
+    """48 requests of the uneven batch (1-16 subdomains, odd and even
+    overlaps, every resident class) over several windows: the resident path
+    and the band kernels take the same number of steps with the same status
+    and the same meshes to rounding; a sample of requests against the
+    oracle."""
+    probs = [p.replace(max_steps=200) for p in W.config4(count=48)]
+    for prec in ("fp64", "fp32"):
+        ps = [p.replace(precision=prec) for p in probs]
+        res = pma.solve_many(ps, window_steps=16, resident=4)
+        band = pma.solve_many(ps, window_steps=16, resident=0)
+        for p, (xr, _, ir), (xb, _, ib) in zip(ps, res, band):
+            assert (ir.steps, ir.status) == (ib.steps, ib.status), (p.n, p.parts)
+            tol = 1e-9 if prec == "fp64" else 1e-4
+            assert np.abs(xr - xb).max() / _size(p) <= tol, (p.n, p.parts)
+    for k in (12, 17, 21):
+        ref = oracle.solve(probs[k].replace(precision="fp64"))
+        x, _, info = pma.solve(probs[k].replace(precision="fp64"), want_psi=False,
+                               window_steps=16, resident=4)
+        assert info.steps == ref.steps and pma.STATUS_NAMES[info.status] == ref.status
+        assert np.abs(x - ref.x).max() / _size(probs[k]) <= TOL64
+
+
+def test_resident_clusters_of_sixteen_and_packing():
+    """Requests with 16, 9, 5, 2 and 1 subdomains packed into clusters of
+    16 CTAs; each mesh bitwise equal to the request solved alone."""
+    probs = []
+    for parts, n in (((4, 4, 1), 96), ((3, 3, 1), 70), ((5, 1, 1), 90), ((1, 2, 1), 40),
+                     ((1, 1, 1), 30), ((2, 2, 1), 50)):
+        nn = (n, n - 7, 1)
+        probs.append(W.Problem(dim=2, n=nn, monitor=W.ring_monitor(), parts=parts,
+                               overlap=4 if parts != (1, 1, 1) else 0, dt=W.dt_for(nn, 2),
+                               tol=0.0, max_steps=90, precision="fp32"))
+    mixed = pma.solve_many(probs, window_steps=20, resident=4)
+    for p, m in zip(probs, mixed):
+        alone = pma.solve(p, want_psi=False, resident=4)
+        assert np.array_equal(alone[0], m[0])
+    ref = oracle.solve(probs[0])
+    assert np.abs(mixed[0][0] - ref.x).max() <= TOL32
 
 
 def test_alone_equals_in_mix():
