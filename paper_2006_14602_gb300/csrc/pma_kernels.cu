@@ -500,10 +500,25 @@ __device__ __forceinline__ void copy16(T* d, const T* s) {
 }
 
 // ---------------------------------------------------------------- 2D stencil
+// Three-input minimum / maximum (one instruction on sm_100-family GPUs for
+// FP32; NaN operands are ignored as by fmin / fmax).
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float min3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ double max3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
+
 // Loop invariants of one 2D subdomain (or band) for one step, in registers.
 template <typename T>
 struct RunK {
-  P2<T> NCL, DT2, M2, ONE, I2H0, I2H1, IH20, IH21, INV4, NINV4;
+  P2<T> NCL, DT2, M2, ONE, I2H0, I2H1, IH20, IH21, INV4, NINV4, BIG, NBIG;
   T c_lag, scale_root, inv_dim, lo0, h0, lo1, h1;
   int nterms;
   bool fast, logrhs, want_l2;
@@ -529,6 +544,8 @@ __device__ __forceinline__ RunK<T> make_runk(const ProbHot<T>& ph, const ProbSta
   K.IH21 = P2<T>::s(ph.invh2[1]);
   K.INV4 = P2<T>::s(ph.inv4hh[0]);
   K.NINV4 = P2<T>::s(-ph.inv4hh[0]);
+  K.BIG = P2<T>::s(big_val<T>());
+  K.NBIG = P2<T>::s(-big_val<T>());
   K.want_l2 = ph.stop_norm == PMA_STOP_L2_INCREMENT;
   K.logrhs = ph.rhs == PMA_RHS_LOG || phase != PH_RUN;
   K.nterms = ph.mon.nterms;
@@ -634,10 +651,20 @@ __device__ __forceinline__ void stencil_run4(const RunK<T>& K, const MonT<T>& mo
       R[pp] = P2<T>::mk(rho_at<T>(mon, X0[pp].x(), X1[pp].x(), T(0)),
                         rho_at<T>(mon, X0[pp].y(), X1[pp].y(), T(0)));
   }
-  T gcv[4], rdv[4];
+  // Masks: 1 at updated nodes, 0 at the others (a transmission row or
+  // column, or beyond the subdomain, where the window may hold stale
+  // values).  The others get rho det := 1 (the one select per node), so
+  // every value below stays finite there, their G - c enters the finiteness
+  // sum as -c_lag, their theta weight is 0 (they are never owned), and
+  // +-big offsets keep them out of the extrema.
+  const P2<T> ROWU = P2<T>::s(rowdir ? T(0) : T(1));
+  const P2<T> WYO = P2<T>::s(wyo);
+  P2<T> GMX[2], GMN[2], DMN[2], GCs[2], Ms[2];
 #pragma unroll
   for (int pp = 0; pp < 2; ++pp) {
-    const P2<T> rD = pmul(R[pp], DD[pp]);
+    const P2<T> m = pmul(P2<T>::mk(uc.v[2 * pp], uc.v[2 * pp + 1]), ROWU);
+    const P2<T> rd = pmul(R[pp], DD[pp]);
+    const P2<T> rD = P2<T>::mk(m.x() != T(0) ? rd.x() : T(1), m.y() != T(0) ? rd.y() : T(1));
     P2<T> GC;
     if (K.logrhs) {
       GC = P2<T>::mk(Fm<T>::ln(rD.x()), Fm<T>::ln(rD.y()));
@@ -649,41 +676,32 @@ __device__ __forceinline__ void stencil_run4(const RunK<T>& K, const MonT<T>& mo
     const P2<T> vn = pfma(GC, K.DT2, P2<T>::mk(wC[2 * pp + 1], wC[2 * pp + 2]));
     o.v[2 * pp] = vn.x();
     o.v[2 * pp + 1] = vn.y();
-    gcv[2 * pp] = GC.x();
-    gcv[2 * pp + 1] = GC.y();
-    rdv[2 * pp] = rD.x();
-    rdv[2 * pp + 1] = rD.y();
+    A.gs2 = padd(A.gs2, GC);
+    A.th2 = pfma(pmul(P2<T>::mk(wc.v[2 * pp], wc.v[2 * pp + 1]), WYO), rD, A.th2);
+    const P2<T> kmx = pfma(m, K.BIG, K.NBIG);  // 0 or -big
+    const P2<T> kmn = pfma(m, K.NBIG, K.BIG);  // 0 or +big
+    GMX[pp] = pfma(GC, m, kmx);
+    GMN[pp] = pfma(GC, m, kmn);
+    DMN[pp] = pfma(DD[pp], m, kmn);
+    GCs[pp] = GC;
+    Ms[pp] = m;
   }
-  const T rowu = rowdir ? T(0) : T(1);
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const bool upd = uc.v[u] * rowu != T(0);
-    const T dv = u < 2 ? (u == 0 ? DD[0].x() : DD[0].y()) : (u == 2 ? DD[1].x() : DD[1].y());
-    A.gcmax = fmax(A.gcmax, upd ? gcv[u] : -big_val<T>());
-    A.gcmin = fmin(A.gcmin, upd ? gcv[u] : big_val<T>());
-    A.dmin = fmin(A.dmin, upd ? dv : big_val<T>());
-    const T g = upd ? gcv[u] : T(0);
-    const T rd = upd ? rdv[u] : T(0);
-    if (u & 1) {
-      A.gs2 = padd(A.gs2, P2<T>::mk(T(0), g));
-      A.th2 = pfma(P2<T>::mk(T(0), wc.v[u] * wyo), P2<T>::mk(T(0), rd), A.th2);
-    } else {
-      A.gs2 = padd(A.gs2, P2<T>::mk(g, T(0)));
-      A.th2 = pfma(P2<T>::mk(wc.v[u] * wyo, T(0)), P2<T>::mk(rd, T(0)), A.th2);
-    }
-    if (!upd) o.v[u] = T(0);
-  }
+  A.gcmax = max3(max3(A.gcmax, GMX[0].x(), GMX[0].y()), GMX[1].x(), GMX[1].y());
+  A.gcmin = min3(min3(A.gcmin, GMN[0].x(), GMN[0].y()), GMN[1].x(), GMN[1].y());
+  A.dmin = min3(min3(A.dmin, DMN[0].x(), DMN[0].y()), DMN[1].x(), DMN[1].y());
   if (K.want_l2) {
     Vec4<T> lc;
     lc.lds(lcp);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const bool upd = uc.v[u] * rowu != T(0);
-      const T w = upd ? lc.v[u] * wly : T(0);
-      const T d = upd ? gcv[u] : T(0);
-      A.l2a = fma(w * d, d, A.l2a);
-      A.l2b = fma(w, d, A.l2b);
-      A.ws += w;
+    for (int pp = 0; pp < 2; ++pp) {
+      const P2<T> w = pmul(pmul(P2<T>::mk(lc.v[2 * pp], lc.v[2 * pp + 1]), P2<T>::s(wly)), Ms[pp]);
+      const P2<T> d = pmul(GCs[pp], Ms[pp]);
+      A.l2a = fma(w.x() * d.x(), d.x(), A.l2a);
+      A.l2b = fma(w.x(), d.x(), A.l2b);
+      A.ws += w.x();
+      A.l2a = fma(w.y() * d.y(), d.y(), A.l2a);
+      A.l2b = fma(w.y(), d.y(), A.l2b);
+      A.ws += w.y();
     }
   }
 }
@@ -1561,6 +1579,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
       const P2<T> IH22 = P2<T>::s(H.ph.invh2[2]);
       const P2<T> I4XY = P2<T>::s(H.ph.inv4hh[0]), I4XZ = P2<T>::s(H.ph.inv4hh[1]);
       const P2<T> I4YZ = P2<T>::s(H.ph.inv4hh[2]);
+      const P2<T> BIG = P2<T>::s(big_val<T>()), NBIG = P2<T>::s(-big_val<T>());
       for (int q = tid; q < nruns; q += NT) {
         const int r = qdiv(q, rpr, inv_rpr), c0 = (q - r * rpr) * 4;
         const int j = j0 + r, gj = g01 + j;
@@ -1661,11 +1680,17 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
               R[pp] = P2<T>::mk(rho_at<T>(H.ph.mon, X0[pp].x(), X1[pp].x(), X2[pp].x()),
                                 rho_at<T>(H.ph.mon, X0[pp].y(), X1[pp].y(), X2[pp].y()));
           }
+          // masks: 1 at updated nodes, 0 elsewhere; no selects per node but
+          // rho det := 1 at the others (see stencil_run4)
           Vec4<T> o;
-          T gcv[4], rdv[4], dv[4];
+          const P2<T> ROWU = P2<T>::s((rowdir || plndir) ? T(0) : T(1));
+          const P2<T> WYZ = P2<T>::s(wyo * wzo);
+          P2<T> GMX[2], GMN[2], DMN[2], GCs[2], Ms[2];
 #pragma unroll
           for (int pp = 0; pp < 2; ++pp) {
-            const P2<T> rD = pmul(R[pp], DD[pp]);
+            const P2<T> m = pmul(P2<T>::mk(uc.v[2 * pp], uc.v[2 * pp + 1]), ROWU);
+            const P2<T> rd = pmul(R[pp], DD[pp]);
+            const P2<T> rD = P2<T>::mk(m.x() != T(0) ? rd.x() : T(1), m.y() != T(0) ? rd.y() : T(1));
             P2<T> GC;
             if (logrhs) {
               GC = padd(P2<T>::mk(Fm<T>::ln(rD.x()), Fm<T>::ln(rD.y())), NCL);
@@ -1676,44 +1701,32 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
             const P2<T> vn = pfma(GC, DT2, P2<T>::mk(cC[2 * pp + 1], cC[2 * pp + 2]));
             o.v[2 * pp] = vn.x();
             o.v[2 * pp + 1] = vn.y();
-            gcv[2 * pp] = GC.x();
-            gcv[2 * pp + 1] = GC.y();
-            rdv[2 * pp] = rD.x();
-            rdv[2 * pp + 1] = rD.y();
-            dv[2 * pp] = DD[pp].x();
-            dv[2 * pp + 1] = DD[pp].y();
+            gs2 = padd(gs2, GC);
+            th2 = pfma(pmul(P2<T>::mk(wc.v[2 * pp], wc.v[2 * pp + 1]), WYZ), rD, th2);
+            const P2<T> kmx = pfma(m, BIG, NBIG), kmn = pfma(m, NBIG, BIG);
+            GMX[pp] = pfma(GC, m, kmx);
+            GMN[pp] = pfma(GC, m, kmn);
+            DMN[pp] = pfma(DD[pp], m, kmn);
+            GCs[pp] = GC;
+            Ms[pp] = m;
           }
-          const T rowu = (rowdir || plndir) ? T(0) : T(1);
-          const T wyz = wyo * wzo;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const bool upd = uc.v[u] * rowu != T(0);
-            gcmax = fmax(gcmax, upd ? gcv[u] : -big_val<T>());
-            gcmin = fmin(gcmin, upd ? gcv[u] : big_val<T>());
-            acc.dmin = fmin(acc.dmin, upd ? dv[u] : big_val<T>());
-            const T g = upd ? gcv[u] : T(0);
-            const T rd = upd ? rdv[u] : T(0);
-            if (u & 1) {
-              gs2 = padd(gs2, P2<T>::mk(T(0), g));
-              th2 = pfma(P2<T>::mk(T(0), wc.v[u] * wyz), P2<T>::mk(T(0), rd), th2);
-            } else {
-              gs2 = padd(gs2, P2<T>::mk(g, T(0)));
-              th2 = pfma(P2<T>::mk(wc.v[u] * wyz, T(0)), P2<T>::mk(rd, T(0)), th2);
-            }
-            if (!upd) o.v[u] = T(0);
-          }
+          gcmax = max3(max3(gcmax, GMX[0].x(), GMX[0].y()), GMX[1].x(), GMX[1].y());
+          gcmin = min3(min3(gcmin, GMN[0].x(), GMN[0].y()), GMN[1].x(), GMN[1].y());
+          acc.dmin = min3(min3(acc.dmin, DMN[0].x(), DMN[0].y()), DMN[1].x(), DMN[1].y());
           if (want_l2) {
             Vec4<T> lc;
             lc.lds(lcol + c0);
             const T wl = ((j == 0 || j == n1 - 1) ? hw1 : h1) * ((kk == 0 || kk == n2 - 1) ? hw2 : h2);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const bool upd = uc.v[u] * rowu != T(0);
-              const T w = upd ? lc.v[u] * wl : T(0);
-              const T d = upd ? gcv[u] : T(0);
-              l2a = fma(w * d, d, l2a);
-              l2b = fma(w, d, l2b);
-              ws += w;
+            for (int pp = 0; pp < 2; ++pp) {
+              const P2<T> w = pmul(pmul(P2<T>::mk(lc.v[2 * pp], lc.v[2 * pp + 1]), P2<T>::s(wl)), Ms[pp]);
+              const P2<T> d = pmul(GCs[pp], Ms[pp]);
+              l2a = fma(w.x() * d.x(), d.x(), l2a);
+              l2b = fma(w.x(), d.x(), l2b);
+              ws += w.x();
+              l2a = fma(w.y() * d.y(), d.y(), l2a);
+              l2b = fma(w.y(), d.y(), l2b);
+              ws += w.y();
             }
           }
           if (run) {
