@@ -79,12 +79,19 @@ typedef struct {
  *                    functions: BURGERS Eq. test_fn1 (eps = p0), SPIRAL
  *                    Eq. test_fn2, TANH_SPHERE Eq. test_fn3d1, NINE_SPHERES
  *                    Eq. test_fn3d2.  nterms is ignored.
+ *   PMA_MON_TABLE   rho sampled on a uniform grid of tn[a] >= 2 points over
+ *                    [tlo[a], thi[a]] per axis a < dim (values x fastest,
+ *                    all > 0 and finite), as a physical solution is sampled
+ *                    in the moving-mesh loop of Sect. 2; evaluated by
+ *                    multilinear interpolation with the point clamped to the
+ *                    table's box.  `table` is host memory, copied at submit;
+ *                    it is stored on the device in the request's precision.
  * The density need not be normalised: the normalisation of Eq. (edp) is
  * applied by the solver (see pma_params.normalize).                        */
 enum { PMA_TERM_BUMP = 0, PMA_TERM_RING = 1, PMA_TERM_SINE = 2, PMA_TERM_BUMP1 = 3 };
 enum { PMA_MON_SUM = 0, PMA_MON_PRODUCT = 1, PMA_MON_ARCLEN_BURGERS = 2,
        PMA_MON_ARCLEN_SPIRAL = 3, PMA_MON_ARCLEN_TANH_SPHERE = 4,
-       PMA_MON_ARCLEN_NINE_SPHERES = 5 };
+       PMA_MON_ARCLEN_NINE_SPHERES = 5, PMA_MON_TABLE = 6 };
 
 typedef struct {
   int32_t type;
@@ -101,6 +108,10 @@ typedef struct {
   double base;
   double p0;
   pma_term term[PMA_MAX_TERMS];
+  const double *table;  /* PMA_MON_TABLE only (else ignored)         */
+  int32_t tn[3];        /* table points per axis (1 on axes >= dim)  */
+  int32_t reserved;
+  double tlo[3], thi[3];
 } pma_monitor;
 
 /* Overlapping decomposition (Sect. 3).  parts[a] subdomains along axis a

@@ -29,7 +29,7 @@ OR_MAX_TERMS = 4
 
 _TERM = {"bump": 0, "ring": 1, "sine": 2, "bump1": 3}
 _KIND = {"sum": 0, "product": 1, "arclen_burgers": 2, "arclen_spiral": 3,
-         "arclen_tanh_sphere": 4, "arclen_nine_spheres": 5}
+         "arclen_tanh_sphere": 4, "arclen_nine_spheres": 5, "table": 6}
 _NORM = {"max_ut": 0, "l2_increment": 1}
 _RULE = {"all": 0, "any": 1}
 _RHS = {"log": 0, "root": 1}
@@ -50,7 +50,9 @@ class _Term(C.Structure):
 
 class _Monitor(C.Structure):
     _fields_ = [("kind", C.c_int), ("nterms", C.c_int), ("base", C.c_double),
-                ("p0", C.c_double), ("term", _Term * OR_MAX_TERMS)]
+                ("p0", C.c_double), ("term", _Term * OR_MAX_TERMS),
+                ("table", C.POINTER(C.c_double)), ("tn", C.c_int * 3),
+                ("tlo", C.c_double * 3), ("thi", C.c_double * 3)]
 
 
 class _Decomp(C.Structure):
@@ -161,6 +163,15 @@ def _monitor(mon) -> _Monitor:
         T.a, T.k = float(t.a), float(t.k)
         for a in range(3):
             T.c[a] = float(t.c[a])
+    if mon.kind == "table":
+        tab = np.ascontiguousarray(mon.table, dtype=np.float64)
+        shape = tab.shape[::-1]  # (tn_x, tn_y[, tn_z])
+        for a in range(3):
+            m.tn[a] = int(shape[a]) if a < len(shape) else 1
+            m.tlo[a] = float(mon.tlo[a])
+            m.thi[a] = float(mon.thi[a])
+        m.table = tab.ctypes.data_as(C.POINTER(C.c_double))
+        m._keep = tab  # the struct holds a raw pointer into this array
     return m
 
 

@@ -127,8 +127,46 @@ static double arclen_rho(const or_monitor *m, const double *x) {
   return sqrt(1.0 + gu[0] * gu[0] + gu[1] * gu[1] + gu[2] * gu[2]);
 }
 
+/* Multilinear interpolation of a tabulated density: along each axis the
+ * point is clamped to [tlo, thi], located in its table cell (the last cell
+ * on the upper face) and weighted by its fractional position; the 2^dim
+ * corner values are combined with the product weights.                     */
+static double table_rho(const or_monitor *m, int dim, const double *x) {
+  long base[3] = {0, 0, 0};
+  double frac[3] = {0.0, 0.0, 0.0};
+  long stride[3];
+  double r = 0.0;
+  int a, corner;
+  stride[0] = 1;
+  stride[1] = m->tn[0];
+  stride[2] = (long)m->tn[0] * m->tn[1];
+  for (a = 0; a < dim; ++a) {
+    const double h = (m->thi[a] - m->tlo[a]) / (double)(m->tn[a] - 1);
+    double s = (x[a] - m->tlo[a]) / h;
+    long k;
+    if (s < 0.0) s = 0.0;
+    if (s > (double)(m->tn[a] - 1)) s = (double)(m->tn[a] - 1);
+    k = (long)floor(s);
+    if (k > m->tn[a] - 2) k = m->tn[a] - 2;
+    base[a] = k;
+    frac[a] = s - (double)k;
+  }
+  for (corner = 0; corner < (1 << dim); ++corner) {
+    double w = 1.0;
+    long idx = 0;
+    for (a = 0; a < dim; ++a) {
+      const int up = (corner >> a) & 1;
+      w *= up ? frac[a] : 1.0 - frac[a];
+      idx += (base[a] + up) * stride[a];
+    }
+    r += w * m->table[idx];
+  }
+  return r;
+}
+
 static double rho_at(const or_monitor *m, int dim, const double *x) {
   int t;
+  if (m->kind == OR_MON_TABLE) return table_rho(m, dim, x);
   if (m->kind == OR_MON_SUM) {
     double r = m->base;
     for (t = 0; t < m->nterms; ++t) r += term_value(&m->term[t], dim, x);

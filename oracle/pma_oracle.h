@@ -53,11 +53,16 @@ typedef struct {
  *   ARCLEN_*: rho = sqrt(1 + |grad u(x)|^2), Eq. (monitfn), with u the test
  *             functions of Sect. 4: BURGERS Eq. (test_fn1) (eps = p0),
  *             SPIRAL Eq. (test_fn2), TANH_SPHERE Eq. (test_fn3d1),
- *             NINE_SPHERES Eq. (test_fn3d2).                                */
+ *             NINE_SPHERES Eq. (test_fn3d2).
+ *   TABLE   : rho given at the nodes of a uniform grid of tn[a] >= 2 points
+ *             on [tlo[a], thi[a]] per axis (x fastest), as a solution
+ *             computed on a physical mesh would be sampled (Sect. 2, the
+ *             moving-mesh loop); evaluated by multilinear interpolation,
+ *             the point first clamped to the table's box.                  */
 enum { OR_TERM_BUMP = 0, OR_TERM_RING = 1, OR_TERM_SINE = 2, OR_TERM_BUMP1 = 3 };
 enum { OR_MON_SUM = 0, OR_MON_PRODUCT = 1, OR_MON_ARCLEN_BURGERS = 2,
        OR_MON_ARCLEN_SPIRAL = 3, OR_MON_ARCLEN_TANH_SPHERE = 4,
-       OR_MON_ARCLEN_NINE_SPHERES = 5 };
+       OR_MON_ARCLEN_NINE_SPHERES = 5, OR_MON_TABLE = 6 };
 
 typedef struct {
   int type;
@@ -72,6 +77,9 @@ typedef struct {
   double base;
   double p0;
   or_term term[OR_MAX_TERMS];
+  const double *table; /* TABLE: tn[0] * tn[1] * tn[2] values, x fastest  */
+  int tn[3];           /* TABLE: points per axis (1 on axes >= dim)      */
+  double tlo[3], thi[3];
 } or_monitor;
 
 /* Overlapping decomposition (Sect. 3): parts[a] subdomains along axis a,

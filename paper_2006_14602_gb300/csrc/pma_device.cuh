@@ -154,8 +154,45 @@ __device__ T arclen_rho(const MonT<T>& m, T x0, T x1, T x2) {
   return Fm<T>::sq(1 + g0 * g0 + g1 * g1 + g2 * g2);
 }
 
+// Tabulated density: multilinear interpolation, the point clamped to the
+// table's box per axis (cell index at most tn - 2), corners combined with
+// product weights in axis order.
+template <typename T>
+__device__ T table_rho(const MonT<T>& m, T x0, T x1, T x2) {
+  const T xs[3] = {x0, x1, x2};
+  int base = 0, stride = 1;
+  int st[3];
+  T f[3];
+  for (int a = 0; a < 3; ++a) {
+    st[a] = stride;
+    f[a] = T(0);
+    if (a < m.dim) {
+      T s = (xs[a] - m.tlo[a]) * m.tsc[a];
+      s = fmin(fmax(s, T(0)), (T)(m.tn[a] - 1));
+      int k = (int)floor(s);
+      k = k > m.tn[a] - 2 ? m.tn[a] - 2 : k;
+      f[a] = s - (T)k;
+      base += k * stride;
+    }
+    stride *= m.tn[a];
+  }
+  T r = T(0);
+  for (int corner = 0; corner < (1 << m.dim); ++corner) {
+    T w = T(1);
+    int idx = base;
+    for (int a = 0; a < m.dim; ++a) {
+      const int up = (corner >> a) & 1;
+      w *= up ? f[a] : T(1) - f[a];
+      idx += up * st[a];
+    }
+    r = fma(w, __ldg(m.table + idx), r);
+  }
+  return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T rho_at(const MonT<T>& m, T x0, T x1, T x2) {
+  if (m.kind == PMA_MON_TABLE) return table_rho<T>(m, x0, x1, x2);
   if (m.kind == PMA_MON_SUM) {
     T r = m.base;
     for (int i = 0; i < kMaxTerms; ++i)

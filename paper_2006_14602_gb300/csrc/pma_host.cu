@@ -64,6 +64,8 @@ struct Request {
   pma_decomp d{};
   pma_params p{};
   std::vector<double> psi0;
+  std::vector<char> tab_dev;  // tabulated density in the request's precision
+  size_t tab_off = 0;
   int dim = 2, cls = 0, esize = 4;
   int parts[3] = {1, 1, 1};
   int bcore[3][kMaxParts + 1];
@@ -83,7 +85,7 @@ struct Request {
 
 // --------------------------------------------------------------- validation
 bool monitor_ok(const pma_monitor& m, int dim) {
-  if (m.kind < PMA_MON_SUM || m.kind > PMA_MON_ARCLEN_NINE_SPHERES) return false;
+  if (m.kind < PMA_MON_SUM || m.kind > PMA_MON_TABLE) return false;
   if ((m.kind == PMA_MON_ARCLEN_BURGERS || m.kind == PMA_MON_ARCLEN_SPIRAL) && dim != 2)
     return false;
   if ((m.kind == PMA_MON_ARCLEN_TANH_SPHERE || m.kind == PMA_MON_ARCLEN_NINE_SPHERES) &&
@@ -99,6 +101,52 @@ bool monitor_ok(const pma_monitor& m, int dim) {
     }
   }
   return true;
+}
+
+// Copy a tabulated density into the request (validated; the caller's memory
+// is not referenced after this) and its device image in the request's
+// precision.
+pma_status take_table(Request& r) {
+  r.tab_dev.clear();
+  if (r.m.kind != PMA_MON_TABLE) {
+    r.m.table = nullptr;
+    return PMA_OK;
+  }
+  const int dim = r.g.dim;
+  long long cnt = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (a >= dim) {
+      r.m.tn[a] = 1;
+      continue;
+    }
+    if (r.m.tn[a] < 2 || r.m.tn[a] > (1 << 16) || !(r.m.thi[a] > r.m.tlo[a])) {
+      set_err("monitor.table: 2 <= tn <= 65536 and thi > tlo on every axis");
+      return PMA_ERR_INVALID;
+    }
+    cnt *= r.m.tn[a];
+  }
+  if (!r.m.table || cnt > (1LL << 28)) {
+    set_err("monitor.table: missing or larger than 2^28 values");
+    return PMA_ERR_INVALID;
+  }
+  const int esize = (r.p.precision == PMA_FP64) ? 8 : 4;
+  r.tab_dev.resize((size_t)cnt * esize);
+  for (long long i = 0; i < cnt; ++i) {
+    const double v = r.m.table[i];
+    if (!(v > 0.0) || !std::isfinite(v)) {
+      r.tab_dev.clear();
+      set_err("monitor.table: values must be positive and finite");
+      return PMA_ERR_INVALID;
+    }
+    if (esize == 8) {
+      memcpy(r.tab_dev.data() + 8 * i, &v, 8);
+    } else {
+      const float f = (float)v;
+      memcpy(r.tab_dev.data() + 4 * i, &f, 4);
+    }
+  }
+  r.m.table = nullptr;
+  return PMA_OK;
 }
 
 // Core partition b_k = round(k N / p); part k spans
@@ -134,8 +182,9 @@ pma_status build_request(Request& r) {
     set_err("params: option out of range");
     return PMA_ERR_INVALID;
   }
-  if (r.d.transmission != PMA_TRANSMISSION_PARALLEL) {
-    set_err("decomp.transmission: only the parallel form runs on the device");
+  if (r.d.transmission != PMA_TRANSMISSION_PARALLEL &&
+      r.d.transmission != PMA_TRANSMISSION_ALTERNATING) {
+    set_err("decomp.transmission: unknown form");
     return PMA_ERR_INVALID;
   }
   if (!monitor_ok(r.m, r.dim)) {
@@ -205,6 +254,8 @@ pma_status build_request(Request& r) {
       }
   r.psi_off = off;
   if (!r.psi0.empty()) off = align(off + (size_t)r.nodes * sizeof(double));
+  r.tab_off = off;
+  if (!r.tab_dev.empty()) off = align(off + r.tab_dev.size());
   r.bytes = off;
   return PMA_OK;
 }
@@ -399,6 +450,7 @@ void fill_hot(const Request& r, const ProbDesc& pd, ProbHot<T>& h) {
   h.stop_norm = pd.stop_norm;
   h.sub_base = pd.sub_base;
   h.ntiles = pd.tile_end - pd.tile_begin;
+  h.alternating = pd.transmission == PMA_TRANSMISSION_ALTERNATING ? 1 : 0;
   for (int a = 0; a < 3; ++a) {
     h.N[a] = pd.N[a];
     h.parts[a] = pd.parts[a];
@@ -419,6 +471,16 @@ void fill_hot(const Request& r, const ProbDesc& pd, ProbHot<T>& h) {
   h.mon.kind = r.m.kind;
   h.mon.nterms = r.m.nterms;
   h.mon.dim = pd.dim;
+  h.mon.table = (r.m.kind == PMA_MON_TABLE && (int)sizeof(T) == r.esize && r.block)
+                    ? (const T*)(r.block + r.tab_off)
+                    : nullptr;
+  for (int a = 0; a < 3; ++a) {
+    h.mon.tn[a] = (a < pd.dim && r.m.kind == PMA_MON_TABLE) ? r.m.tn[a] : 1;
+    h.mon.tlo[a] = (T)r.m.tlo[a];
+    h.mon.tsc[a] = (a < pd.dim && r.m.kind == PMA_MON_TABLE)
+                       ? (T)((double)(r.m.tn[a] - 1) / (r.m.thi[a] - r.m.tlo[a]))
+                       : T(0);
+  }
   h.mon.base = (T)r.m.base;
   h.mon.p0 = (T)r.m.p0;
   for (int t = 0; t < kMaxTerms; ++t) {
@@ -889,6 +951,11 @@ pma_status admit(pma_ctx* c) {
     }
     r.block = (char*)blk;
     c->used += r.bytes;
+    if (!r.tab_dev.empty()) {
+      PMA_CK(cudaMemcpyAsync(r.block + r.tab_off, r.tab_dev.data(), r.tab_dev.size(),
+                             cudaMemcpyHostToDevice, c->stream));
+      c->stats.h2d_bytes += (double)r.tab_dev.size();
+    }
     if (!r.psi0.empty()) {
       PMA_CK(cudaMemcpyAsync(r.block + r.psi_off, r.psi0.data(), sizeof(double) * r.nodes,
                              cudaMemcpyHostToDevice, c->stream));
@@ -1164,7 +1231,9 @@ pma_status pma_submit(pma_ctx* c, const pma_grid* grid, const pma_monitor* mon,
     if (n <= 0) return PMA_ERR_INVALID;
     r->psi0.assign(psi0, psi0 + n);
   }
-  pma_status st = build_request(*r);
+  pma_status st = take_table(*r);
+  if (st != PMA_OK) return st;
+  st = build_request(*r);
   if (st != PMA_OK) return st;
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->budget && r->bytes > c->budget) {
@@ -1548,7 +1617,9 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
     r.d.transmission = PMA_TRANSMISSION_PARALLEL;
   }
   r.p = *par;
-  pma_status st = build_request(r);  // state layout (no warm start block)
+  pma_status st = take_table(r);
+  if (st != PMA_OK) return st;
+  st = build_request(r);  // state layout (no warm start block)
   if (st != PMA_OK) return st;
   int dev = 0;
   PMA_CK(cudaGetDevice(&dev));
@@ -1632,6 +1703,9 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   PMA_CK(cudaMemcpyAsync(B + o_hotf, &hf, sizeof(hf), cudaMemcpyHostToDevice, s));
   PMA_CK(cudaMemcpyAsync(B + o_hotd, &hd, sizeof(hd), cudaMemcpyHostToDevice, s));
   PMA_CK(cudaMemcpyAsync(B + o_st, &ps, sizeof(ps), cudaMemcpyHostToDevice, s));
+  if (!r.tab_dev.empty())
+    PMA_CK(cudaMemcpyAsync(r.block + r.tab_off, r.tab_dev.data(), r.tab_dev.size(),
+                           cudaMemcpyHostToDevice, s));
   PMA_CK(cudaMemcpyAsync(B + o_fin, &fin, sizeof(fin), cudaMemcpyHostToDevice, s));
   PMA_CK(cudaMemsetAsync(B + o_q, 0, sizeof(unsigned int) * 2 * NUM_CLS, s));
   PMA_CK(cudaStreamSynchronize(s));

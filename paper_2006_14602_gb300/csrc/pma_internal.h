@@ -50,6 +50,11 @@ struct alignas(16) MonT {
     T amp, width, r2, a, k2;
     T c[3];
   } t[kMaxTerms];
+  // PMA_MON_TABLE: device copy in the sweep precision (null for the other
+  // precision), points per axis, box origin and points per unit length
+  const T* table;
+  int tn[3], pad2;
+  T tlo[3], tsc[3];
 };
 
 // Everything one sweep tile needs about its problem, in its precision,
@@ -59,6 +64,7 @@ struct alignas(16) ProbHot {
   int dim, rhs, normalize, stop_norm;
   int N[3], sub_base;
   int parts[3], ntiles;
+  int alternating, pad1[3];  // 1: alternating transmission (Algorithm 1)
   T lo[3], h[3], inv2h[3], invh2[3], inv4hh[3], hw[3];
   T dt, vol;
   double hd[3];

@@ -341,6 +341,52 @@ __device__ __forceinline__ T gather_owner(const LaunchArgs& a, const SmemHdr<T>&
   return __ldcg(ov + ox + pitch * (oy + on1 * oz));
 }
 
+// Alternating transmission (Algorithm 1): a transmission node whose owner
+// precedes its subdomain in raster order takes the owner's value of the
+// current state (already updated this step), read lazily when the box is
+// staged.  Overwrites every such position of a staged box (rows of SWp
+// elements, SHY rows per plane, SHZ planes; column c holds local i0 + c - 4;
+// halo columns 3 / cols + 4 on physical faces are mirror images) with the
+// owner's value of buffer `parity` (no offset correction: the owner's
+// updated nodes carry the same offset as this subdomain's).
+template <typename T, int NT>
+__device__ void stage_alternating(const LaunchArgs& a, const SmemHdr<T>& S, T* sv, int SWp,
+                                  int SHY, int SHZ, int i0, int j0, int k0, int cols) {
+  const SubDesc& sd = S.sd;
+  const int n0 = sd.n[0], n1 = sd.n[1], n2 = sd.n[2], faces = sd.faces, dim = S.ph.dim;
+  const bool plx = faces & 1, phx = faces & 2, ply = faces & 4, phy = faces & 8;
+  const bool plz = faces & 16, phz = faces & 32;
+  const int dlx = plx ? -1 : 0, dhx = phx ? -1 : n0 - 1;
+  const int dly = ply ? -1 : 0, dhy = phy ? -1 : n1 - 1;
+  const int dlz = (dim > 2 && !plz) ? 0 : -1, dhz = (dim > 2 && !phz) ? n2 - 1 : -1;
+  const bool left = (i0 == 0), right = (i0 + cols == n0);
+  const int PS = SHY * SWp;
+  for (int rr = threadIdx.x; rr < SHY * SHZ; rr += NT) {
+    const int lz = rr / SHY, ly = rr - lz * SHY;
+    const int jj = reflect_clamp(j0 - 1 + ly, n1, ply, phy);
+    const int kk = dim > 2 ? reflect_clamp(k0 - 1 + lz, n2, plz, phz) : 0;
+    const bool drow = (jj == dly || jj == dhy || kk == dlz || kk == dhz);
+    for (int c = 3; c <= cols + 4; ++c) {
+      if (left && c == 3 && !plx) continue;          // halo beyond a transmission face
+      if (right && c == cols + 4 && !phx) continue;  // (never read by an updated node)
+      const int ii = reflect_clamp(i0 + c - 4, n0, plx, phx);
+      if (!(drow || ii == dlx || ii == dhx)) continue;
+      const int kx = sd.k[0] + (ii < sd.clo[0] ? -1 : (ii > sd.chi[0] ? 1 : 0));
+      const int ky = sd.k[1] + (jj < sd.clo[1] ? -1 : (jj > sd.chi[1] ? 1 : 0));
+      const int kz = sd.k[2] + (kk < sd.clo[2] ? -1 : (kk > sd.chi[2] ? 1 : 0));
+      const int oidx = (kz * S.ph.parts[1] + ky) * S.ph.parts[0] + kx;
+      if (oidx >= sd.idx) continue;
+      const SubDesc* od = a.subs + S.ph.sub_base + oidx;
+      const int ox = sd.g0[0] + ii - __ldg(&od->g0[0]);
+      const int oy = sd.g0[1] + jj - __ldg(&od->g0[1]);
+      const int oz = sd.g0[2] + kk - __ldg(&od->g0[2]);
+      const long long opitch = __ldg(&od->pitch), on1 = __ldg(&od->n[1]);
+      const T* ov = (const T*)od->v[S.ps.parity];
+      sv[lz * PS + ly * SWp + c] = __ldcg(ov + ox + opitch * (oy + on1 * oz));
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T init_value(const SmemHdr<T>& S, const double* psi0, int gi, int gj,
                                         int gl) {
@@ -888,6 +934,10 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
             for (int c = tid; c < SWp; c += NT)
               if (!(left && c == 3) && !(right && c == cols + 4)) sv[r * SWp + c] += corr;
         }
+      }
+      if (H.ph.alternating) {
+        __syncthreads();
+        stage_alternating<T, NT>(a, H, sv, SWp, SH, 1, i0, j0, 0, cols);
       }
       __syncthreads();  // S2: band staged
       const T c_lag = (T)H.ps.c_lag;
@@ -1540,6 +1590,10 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
           }
         }
       }
+      if (H.ph.alternating) {
+        __syncthreads();
+        stage_alternating<T, NT>(a, H, sv, SWp, SHY, SHZ, i0, j0, k0, cols);
+      }
       const T c_lag = (T)H.ps.c_lag, dt = H.ph.dt;
       const T scale_root = (T)(H.ph.vol / (T)H.ps.theta_prev);
       const T lo0 = H.ph.lo[0], lo1 = H.ph.lo[1], lo2 = H.ph.lo[2];
@@ -1798,7 +1852,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
 // ---------------------------------------------------------------- dispatch
 // Compiled shapes.  2D: (threads, band nodes FP32, band nodes FP64); the
 // staged band plus halo is at most 3x the band nodes.  3D: (TX, TY, TZ).
-#define PMA_T2D(X) X(256, 2048, 1024) X(128, 1024, 512) X(256, 1024, 1024) X(512, 3072, 1536)
+#define PMA_T2D(X) X(128, 1024, 512) X(256, 2048, 1024) X(256, 1024, 1024) X(512, 3072, 1536)
 // 3D: (threads, nodes per plane box, planes FP32, planes FP64, dynamic
 // shared memory in KiB for the staged box and the column tables).
 #define PMA_T3D(X) X(128, 512, 8, 4, 64) X(128, 512, 16, 8, 96) X(256, 1024, 8, 4, 96)
@@ -2006,16 +2060,34 @@ cudaError_t launch_res2d(bool fp64, int id, const ResArgs& a, int nclusters, int
 // Owner-takes combination: global node g takes x = xi + grad_h v of the
 // subdomain whose core holds it (mirror ghost on faces of Omega_c, i.e.
 // x_a = xi_a on faces normal to a), and Psi = v - S + |xi|^2/2.
+// A transmission node carries the previous step's offset (corr is added),
+// except under alternating transmission when its owner precedes the
+// subdomain: then the owner's current value is the node's value.
 template <typename T>
 __device__ __forceinline__ T fetch_v(const SubDesc& sd, const T* v, int dim, int i, int j, int l,
-                                     double corr) {
+                                     double corr, const ProbDesc& pd, const SubDesc* subs,
+                                     int parity) {
   const int n0 = sd.n[0], n1 = sd.n[1], n2 = sd.n[2];
   i = reflect_clamp(i, n0, sd.faces & 1, sd.faces & 2);
   j = dim > 1 ? reflect_clamp(j, n1, sd.faces & 4, sd.faces & 8) : 0;
   l = dim > 2 ? reflect_clamp(l, n2, sd.faces & 16, sd.faces & 32) : 0;
-  T val = v[(long long)i + (long long)sd.pitch * (j + (long long)n1 * l)];
-  if (is_dir(sd.faces, dim, i, j, l, n0, n1, n2)) val += (T)corr;
-  return val;
+  if (is_dir(sd.faces, dim, i, j, l, n0, n1, n2)) {
+    if (pd.transmission == PMA_TRANSMISSION_ALTERNATING) {
+      const int kx = sd.k[0] + (i < sd.clo[0] ? -1 : (i > sd.chi[0] ? 1 : 0));
+      const int ky = sd.k[1] + (j < sd.clo[1] ? -1 : (j > sd.chi[1] ? 1 : 0));
+      const int kz = sd.k[2] + (l < sd.clo[2] ? -1 : (l > sd.chi[2] ? 1 : 0));
+      const int oidx = (kz * pd.parts[1] + ky) * pd.parts[0] + kx;
+      if (oidx < sd.idx) {
+        const SubDesc& od = subs[pd.sub_base + oidx];
+        const T* ov = (const T*)od.v[parity];
+        return ov[(long long)(sd.g0[0] + i - od.g0[0]) +
+                  (long long)od.pitch * ((sd.g0[1] + j - od.g0[1]) +
+                                         (long long)od.n[1] * (sd.g0[2] + l - od.g0[2]))];
+      }
+    }
+    return v[(long long)i + (long long)sd.pitch * (j + (long long)n1 * l)] + (T)corr;
+  }
+  return v[(long long)i + (long long)sd.pitch * (j + (long long)n1 * l)];
 }
 
 template <typename T>
@@ -2044,8 +2116,8 @@ __device__ void combine_node(const CombineJob& J, long long g, const SubDesc* su
       int p[3] = {li[0], li[1], li[2]}, m[3] = {li[0], li[1], li[2]};
       p[a] += 1;
       m[a] -= 1;
-      const T vp = fetch_v<T>(sd, v, dim, p[0], p[1], p[2], ps.corr);
-      const T vm = fetch_v<T>(sd, v, dim, m[0], m[1], m[2], ps.corr);
+      const T vp = fetch_v<T>(sd, v, dim, p[0], p[1], p[2], ps.corr, pd, subs, ps.parity);
+      const T vm = fetch_v<T>(sd, v, dim, m[0], m[1], m[2], ps.corr, pd, subs, ps.parity);
       xa = xi + (double)(vp - vm) * (0.5 / pd.h[a]);
     }
     if (J.out_fp64)
@@ -2126,7 +2198,8 @@ __device__ void node_x_and_hessian(const SubDesc* subs, const ProbDesc& pd, cons
   const T* v = (const T*)sd.v[ps.parity];
   const int li[3] = {gg[0] - sd.g0[0], gg[1] - sd.g0[1], gg[2] - sd.g0[2]};
   auto f = [&](int di, int dj, int dl) -> double {
-    return (double)fetch_v<T>(sd, v, dim, li[0] + di, li[1] + dj, li[2] + dl, ps.corr);
+    return (double)fetch_v<T>(sd, v, dim, li[0] + di, li[1] + dj, li[2] + dl, ps.corr, pd, subs,
+                              ps.parity);
   };
   const double vc = f(0, 0, 0);
   int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};

@@ -50,7 +50,7 @@ PMA_LAUNCH_PER_SUBDOMAIN = 1
 
 _TERM = {"bump": 0, "ring": 1, "sine": 2, "bump1": 3}
 _KIND = {"sum": 0, "product": 1, "arclen_burgers": 2, "arclen_spiral": 3,
-         "arclen_tanh_sphere": 4, "arclen_nine_spheres": 5}
+         "arclen_tanh_sphere": 4, "arclen_nine_spheres": 5, "table": 6}
 _NORM = {"max_ut": 0, "l2_increment": 1}
 _RULE = {"all": 0, "any": 1}
 _RHS = {"log": 0, "root": 1}
@@ -72,7 +72,9 @@ class pma_term(C.Structure):
 
 class pma_monitor(C.Structure):
     _fields_ = [("kind", C.c_int32), ("nterms", C.c_int32), ("base", C.c_double),
-                ("p0", C.c_double), ("term", pma_term * PMA_MAX_TERMS)]
+                ("p0", C.c_double), ("term", pma_term * PMA_MAX_TERMS),
+                ("table", C.POINTER(C.c_double)), ("tn", C.c_int32 * 3),
+                ("reserved", C.c_int32), ("tlo", C.c_double * 3), ("thi", C.c_double * 3)]
 
 
 class pma_decomp(C.Structure):
@@ -337,6 +339,15 @@ def to_structs(prob):
                                           float(t.a), float(t.k))
         for a in range(3):
             T.c[a] = float(t.c[a])
+    if mon.kind == "table":
+        tab = np.ascontiguousarray(mon.table, dtype=np.float64)
+        shape = tab.shape[::-1]  # (n_x, n_y[, n_z])
+        for a in range(3):
+            m.tn[a] = int(shape[a]) if a < len(shape) else 1
+            m.tlo[a] = float(mon.tlo[a])
+            m.thi[a] = float(mon.thi[a])
+        m.table = tab.ctypes.data_as(C.POINTER(C.c_double))
+        m._keep = tab  # copied by the library at submit
     d = pma_decomp()
     for a in range(3):
         d.parts[a] = int(prob.parts[a]) if a < prob.dim else 1

@@ -58,6 +58,11 @@ class Monitor:
     base: float = 1.0
     terms: List[Term] = field(default_factory=list)
     p0: float = 0.0
+    # kind "table": density values on a uniform grid over [tlo, thi], array
+    # shaped (n_y, n_x) or (n_z, n_y, n_x)
+    table: Optional[np.ndarray] = field(default=None, compare=False, repr=False)
+    tlo: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    thi: Tuple[float, float, float] = (1.0, 1.0, 1.0)
 
 
 @dataclass

@@ -159,6 +159,74 @@ def test_monitor_kinds_3d(mon):
     _check(prob)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,n,parts,o", [(2, (45, 37, 1), (3, 2, 1), 5),
+                                           (2, (21, 40, 1), (2, 3, 1), 2),
+                                           (3, (19, 17, 15), (2, 2, 2), 4),
+                                           (3, (16, 24, 18), (1, 3, 2), 2)])
+def test_alternating_transmission(prec, dim, n, parts, o):
+    """Algorithm 1's alternating form: a transmission node whose owner
+    precedes its subdomain takes the owner's new value.  Overlap 2 puts
+    transmission nodes next to owned nodes, so the combination reads them
+    too."""
+    cfl = 0.1 if dim == 2 else 0.05
+    mon = W.ring_monitor() if dim == 2 else W.shell_monitor()
+    prob = W.Problem(dim=dim, n=n, monitor=mon, parts=parts, overlap=o, alternating=1,
+                     dt=W.dt_for(n, dim, cfl=cfl), tol=0.0, max_steps=90 if dim == 2 else 40,
+                     precision=prec)
+    ref = oracle.solve(prob)
+    par = oracle.solve(prob.replace(alternating=0))
+    # the two transmission forms really differ on this problem
+    assert np.abs(ref.x - par.x).max() > 1e-9
+    _check(prob, ref)
+
+
+def test_alternating_converges_at_the_oracle_step():
+    prob = W.Problem(dim=2, n=(33, 33, 1), monitor=W.ring_monitor(), parts=(2, 2, 1), overlap=4,
+                     alternating=1, dt=1e-4, tol=1e-6, max_steps=6000, precision="fp64")
+    x, p, info, ref, err = _check(prob)
+    assert info.status == pma.PMA_OK
+
+
+def _sampled(mon, dim, nt, lo=0.0, hi=1.0):
+    """The density `mon` sampled by the oracle on an nt^dim table."""
+    g = np.linspace(lo, hi, nt)
+    grids = np.meshgrid(*([g] * dim), indexing="ij")[::-1]  # x fastest
+    pts = np.stack([q.ravel() for q in grids], 1)
+    vals = oracle.monitor_eval(mon, dim, pts).reshape((nt,) * dim)
+    return W.Monitor(kind="table", table=vals, tlo=(lo,) * 3, thi=(hi,) * 3)
+
+
+@pytest.mark.parametrize("resident", [0, 4])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tabulated_density_2d(prec, resident):
+    """A density given as a table (sampled from the ring on a 97^2 grid,
+    coarser than nothing else in the problem) through the same path."""
+    mon = _sampled(W.ring_monitor(), 2, 97)
+    prob = W.Problem(dim=2, n=(45, 37, 1), monitor=mon, parts=(3, 2, 1), overlap=5,
+                     dt=W.dt_for((45, 37, 1), 2), tol=0.0, max_steps=120, precision=prec)
+    _check(prob, resident=resident)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tabulated_density_3d(prec):
+    mon = _sampled(W.shell_monitor(), 3, 25)
+    prob = W.Problem(dim=3, n=(19, 17, 15), monitor=mon, parts=(2, 2, 2), overlap=4,
+                     dt=W.dt_for((19, 17, 15), 3, cfl=0.05), tol=0.0, max_steps=40,
+                     precision=prec)
+    _check(prob)
+
+
+def test_tabulated_density_is_validated():
+    bad = np.ones((9, 9))
+    bad[3, 4] = 0.0
+    prob = W.Problem(dim=2, n=(21, 21, 1), monitor=W.Monitor(kind="table", table=bad),
+                     dt=1e-4, tol=0.0, max_steps=5)
+    with pytest.raises(pma.PmaError) as e:
+        pma.solve(prob)
+    assert e.value.status == pma.PMA_ERR_INVALID and "table" in pma.pma_last_error()
+
+
 # ------------------------------------------------------------------ modes
 
 def test_launch_modes_are_bitwise_identical():

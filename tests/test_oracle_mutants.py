@@ -36,6 +36,8 @@ PINS = [
     ("equidist1d", P.test_1d_steady_state_equidistributes),
     ("dd_steady", lambda: P.test_dd_steady_state_equals_single_domain(0)),
     ("overlap", P.test_dd_error_decreases_with_overlap),
+    ("table", P.test_table_monitor_is_exact_on_multilinear_densities),
+    ("alternating", lambda: P.test_dd_steady_state_equals_single_domain(1)),
 ]
 
 MUTANTS = {
@@ -67,6 +69,11 @@ MUTANTS = {
                              "long b0 = ((long)k * n) / parts + 1;"),
     "owner_output_from_first": ("int o = owner_of(d, gidx);\n        const sub_t *s = &d->sub[o];",
                                 "int o = 0;\n        const sub_t *s = &d->sub[o];"),
+    "table_weights_swapped": ("w *= up ? frac[a] : 1.0 - frac[a];",
+                              "w *= up ? 1.0 - frac[a] : frac[a];"),
+    "table_not_clamped": ("if (s > (double)(m->tn[a] - 1)) s = (double)(m->tn[a] - 1);",
+                          ""),
+    "table_cell_stride": ("stride[1] = m->tn[0];", "stride[1] = m->tn[1];"),
 }
 
 

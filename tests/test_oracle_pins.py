@@ -462,3 +462,69 @@ def test_quality_measure_magnitude_matches_paper_table():
         e2s.append(e2)
         assert abs(e2 - gold[str(n)]["E2"]) < 0.01
     assert e2s[1] < e2s[0]
+
+
+# ------------------------------------------------------------------ tabulated density
+
+def _table_monitor(values, tlo, thi):
+    return W.Monitor(kind="table", table=np.asarray(values, dtype=np.float64),
+                     tlo=tuple(tlo) + (0.0,) * (3 - len(tlo)),
+                     thi=tuple(thi) + (1.0,) * (3 - len(thi)))
+
+
+def test_table_monitor_is_exact_on_multilinear_densities():
+    """Multilinear interpolation reproduces a multilinear density exactly
+    (inside the box), and outside it takes the value at the clamped point."""
+    rng = np.random.default_rng(5)
+    # 2D: rho = 2 + x + 3y + 0.5 x y on a 7 x 9 table over [-0.1, 1.2] x [0, 1.1]
+    f2 = lambda x, y: 2.0 + x + 3.0 * y + 0.5 * x * y
+    xs, ys = np.linspace(-0.1, 1.2, 7), np.linspace(0.0, 1.1, 9)
+    tab = f2(xs[None, :], ys[:, None])
+    mon = _table_monitor(tab, (-0.1, 0.0), (1.2, 1.1))
+    pts = rng.uniform([-0.1, 0.0], [1.2, 1.1], size=(200, 2))
+    got = oracle.monitor_eval(mon, 2, pts)
+    assert np.abs(got - f2(pts[:, 0], pts[:, 1])).max() < 1e-13
+    out = np.array([[-0.5, 0.3], [1.7, 2.0], [0.4, -1.0]])
+    clamped = np.clip(out, [-0.1, 0.0], [1.2, 1.1])
+    assert np.abs(oracle.monitor_eval(mon, 2, out) - f2(clamped[:, 0], clamped[:, 1])).max() < 1e-13
+    # 3D: a trilinear density on a 5 x 4 x 6 table
+    f3 = lambda x, y, z: 1 + x + 2 * y + 3 * z + x * y + y * z + x * z + x * y * z
+    gx, gy, gz = np.linspace(0, 1, 5), np.linspace(0, 1, 4), np.linspace(0, 1, 6)
+    tab3 = f3(gx[None, None, :], gy[None, :, None], gz[:, None, None])
+    mon3 = _table_monitor(tab3, (0, 0, 0), (1, 1, 1))
+    pts3 = rng.uniform(0, 1, size=(200, 3))
+    got3 = oracle.monitor_eval(mon3, 3, pts3)
+    assert np.abs(got3 - f3(pts3[:, 0], pts3[:, 1], pts3[:, 2])).max() < 1e-13
+
+
+def test_table_monitor_matches_scipy_linear_interpolation():
+    """A random positive table against scipy's regular-grid linear
+    interpolator (an independent library routine)."""
+    interp = pytest.importorskip("scipy.interpolate")
+    rng = np.random.default_rng(6)
+    for dim, shape in ((2, (11, 8)), (3, (5, 7, 6))):
+        tab = rng.uniform(0.5, 3.0, size=shape)            # (n_z, n_y, n_x) order
+        lo, hi = rng.uniform(-1, 0, size=dim), rng.uniform(1, 2, size=dim)
+        axes = [np.linspace(lo[a], hi[a], shape[::-1][a]) for a in range(dim)]
+        f = interp.RegularGridInterpolator(axes, np.transpose(tab), method="linear")
+        pts = rng.uniform(lo, hi, size=(300, dim))
+        got = oracle.monitor_eval(_table_monitor(tab, lo, hi), dim, pts)
+        assert np.abs(got - f(pts)).max() < 1e-13
+
+
+def test_tabulated_ring_converges_to_the_analytic_ring():
+    """The mesh of a ring density sampled on finer and finer tables tends to
+    the mesh of the analytic ring at second order in the table spacing."""
+    base = W.Problem(dim=2, n=(33, 33, 1), monitor=W.ring_monitor(), dt=W.dt_for((33, 33, 1), 2),
+                     tol=0.0, max_steps=150)
+    ref = oracle.solve(base).x
+    errs = []
+    for nt in (33, 65, 129):
+        g = np.linspace(0.0, 1.0, nt)
+        X, Y = np.meshgrid(g, g, indexing="xy")
+        vals = oracle.monitor_eval(W.ring_monitor(), 2, np.stack([X.ravel(), Y.ravel()], 1))
+        mon = _table_monitor(vals.reshape(nt, nt), (0, 0), (1, 1))
+        errs.append(np.abs(oracle.solve(base.replace(monitor=mon)).x - ref).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert errs[2] < errs[1] < errs[0]
+    assert 3.0 < r1 < 5.5 and 3.0 < r2 < 5.5, (errs, r1, r2)

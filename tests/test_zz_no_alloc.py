@@ -39,6 +39,9 @@ CASES = {
                             overlap=8, dt=W.dt_for((97, 65, 1), 2), tol=0.0, max_steps=120,
                             precision="fp32"),
     "2d_converging": W.config1().replace(max_steps=4000),
+    "2d_alternating": W.Problem(dim=2, n=(40, 33, 1), monitor=W.ring_monitor(), parts=(2, 2, 1),
+                                overlap=2, alternating=1, dt=W.dt_for((40, 33, 1), 2), tol=0.0,
+                                max_steps=100, precision="fp64"),
     "3d_dd_fp64": W.Problem(dim=3, n=(19, 17, 15), monitor=W.shell_monitor(), parts=(2, 2, 2),
                             overlap=4, dt=W.dt_for((19, 17, 15), 3, cfl=0.05), tol=0.0,
                             max_steps=60, precision="fp64"),
