@@ -58,8 +58,11 @@ WORKLOADS = {
 def serving(args):
     """Serving stream: Poisson arrivals of mixed 2D / 3D requests submitted
     from a host thread to a context whose server thread batches them
-    continuously; the same stream on the plain FP64 path (one launch per
-    subdomain and step, no graphs) for comparison."""
+    continuously.  First the whole stream at once (saturation throughput),
+    then Poisson rates of 0.25x..1.5x that throughput (latency under load),
+    a run with a small memory budget (admission back-pressure), and the
+    first requests on the plain FP64 path (one launch per subdomain and
+    step, no graphs) for comparison."""
     import torch
     from paper_2006_14602_gb300 import build, pma
 
@@ -67,12 +70,12 @@ def serving(args):
     pma.load()
     torch.cuda.init()
 
-    def run(stream, precision, plain):
+    def run(stream, precision, plain, budget=120 << 30):
         reqs = [(t, p.replace(precision=precision)) for t, p in stream]
         opts = {"window_steps": args.window, "resident": args.resident}
         if plain:
             opts.update(launch_mode=pma.PMA_LAUNCH_PER_SUBDOMAIN, use_graphs=0)
-        with pma.Context(0, 120 << 30, **opts) as ctx:
+        with pma.Context(0, budget, **opts) as ctx:
             if pma.pma_serve_start(ctx.h) != pma.PMA_OK:
                 raise RuntimeError("server did not start")
             ids = []
@@ -90,32 +93,45 @@ def serving(args):
                 _, info = pma.pma_get_info(ctx.h, i)
                 lat.append(info.latency_us / 1e3)
                 nu += info.steps * _sub_nodes(p)
+                pma.pma_release(ctx.h, i)
             wall = time.perf_counter() - t0
             pma.pma_serve_stop(ctx.h)
-            for i in ids:
-                pma.pma_release(ctx.h, i)
         return {"meshes_per_s": len(reqs) / wall, "node_updates_per_s": nu / wall,
                 "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99),
                 "wall_s": wall, "requests": len(reqs)}
 
-    stream = W.config5_stream(count=args.requests, rate_hz=args.rate, max_steps=args.max_steps or 2000,
-                              size2d=(33, args.max2d), size3d=(17, args.max3d))
+    def stream_at(rate):
+        return W.config5_stream(count=args.requests, rate_hz=rate,
+                                max_steps=args.max_steps or 2000,
+                                size2d=(33, args.max2d), size3d=(17, args.max3d))
+
     warm = W.config5_stream(seed=1, count=4, rate_hz=1e6, max_steps=50, size2d=(33, 65),
                             size3d=(17, 21))
     run(warm, "fp32", False)
-    fp32 = run(stream, "fp32", False)
-    plain = run(stream[: args.plain_requests], "fp64", True) if args.plain_requests else None
+    sat = run(stream_at(1e9), "fp32", False)
+    rates = [args.rate] if args.rate else [f * sat["meshes_per_s"] for f in (0.25, 0.5, 1.0, 1.5)]
+    sweep = []
+    for r in rates:
+        q = run(stream_at(r), "fp32", False)
+        q["rate_per_s"] = r
+        sweep.append(q)
+    small = run(stream_at(rates[-1] if args.rate else sat["meshes_per_s"]), "fp32", False,
+                budget=args.budget_mb << 20)
+    small["budget_mb"] = args.budget_mb
+    plain = run(stream_at(1e9)[: args.plain_requests], "fp64", True) if args.plain_requests else None
     line = {
-        "metric": "meshes/s (serving stream)", "value": fp32["meshes_per_s"], "unit": "meshes/s",
+        "metric": "meshes/s (serving stream)", "value": sat["meshes_per_s"], "unit": "meshes/s",
         "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded Poisson stream, master seed %d)" % W.MASTER_SEED,
-        "config": {"workload": "serving stream: Poisson arrivals at %.1f/s of mixed 2D (33^2-%d^2) "
-                               "and 3D (17^3-%d^3) requests, 1-27 subdomains, random bump "
-                               "monitors, tol 1e-6 or %d steps" % (args.rate, args.max2d,
-                                                                   args.max3d, args.max_steps or 2000),
-                   "requests": len(stream)},
-        "latency_ms": {"p50": fp32["p50_ms"], "p99": fp32["p99_ms"]},
-        "node_updates_per_s": fp32["node_updates_per_s"],
+        "config": {"workload": "serving stream: %d mixed 2D (33^2-%d^2) and 3D (17^3-%d^3) "
+                               "requests, 1-27 subdomains, random bump monitors, tol 1e-6 or "
+                               "%d steps; value = all submitted at once"
+                               % (args.requests, args.max2d, args.max3d, args.max_steps or 2000),
+                   "requests": args.requests},
+        "latency_ms": {"p50": sat["p50_ms"], "p99": sat["p99_ms"]},
+        "node_updates_per_s": sat["node_updates_per_s"],
+        "poisson_sweep": sweep,
+        "small_budget": small,
         "plain_fp64_per_subdomain": plain,
     }
     print(json.dumps(line))
@@ -454,7 +470,10 @@ def main():
     ap.add_argument("--resident", type=int, default=0,
                     help="k > 0: cluster-resident path for 2D requests that fit the "
                          "first k shared-memory classes (0: band kernels only)")
-    ap.add_argument("--rate", type=float, default=20.0, help="c5: arrivals per second")
+    ap.add_argument("--rate", type=float, default=None,
+                    help="c5: one Poisson rate (default: 0.25x..1.5x the saturation throughput)")
+    ap.add_argument("--budget-mb", type=int, default=16,
+                    help="c5: memory budget of the back-pressure run")
     ap.add_argument("--requests", type=int, default=64, help="c5: requests in the stream")
     ap.add_argument("--plain-requests", type=int, default=16,
                     help="c5: requests of the stream replayed on the plain FP64 path")

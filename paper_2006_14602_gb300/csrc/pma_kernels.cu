@@ -878,6 +878,25 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
         }
       }
       cp_async_commit();
+      // Per-column tables of the band (after the staged rows in shared
+      // memory): theta weight of owned columns (0 elsewhere), 1 for updated
+      // columns (inside the band, not a transmission column), and the local
+      // trapezoid weight for the L2 increment.
+      const int cr = (cols + 3) & ~3;
+      {
+      const T h0 = H.ph.h[0], hw0 = H.ph.hw[0];
+      const int N0 = H.ph.N[0], clo0 = H.sd.clo[0], chi0 = H.sd.chi[0];
+      T* const wcol = sv + SH * SWp;
+      T* const ucol = wcol + cr;
+      T* const lcol = ucol + cr;
+      for (int c = tid; c < cr; c += NT) {
+        const int i = i0 + c, gi = g00 + i;
+        const bool valid = c < cols;
+        wcol[c] = (valid && i >= clo0 && i <= chi0) ? ((gi == 0 || gi == N0 - 1) ? hw0 : h0) : T(0);
+        ucol[c] = (valid && i != dlx && i != dhx) ? T(1) : T(0);
+        lcol[c] = (i == 0 || i == n0 - 1) ? hw0 : h0;
+      }
+      }
       // (b) halo columns on the subdomain's x faces (Neumann mirror; clamp on
       //     transmission faces, where the value is never used): loaded now,
       //     written after the copies land.  At most 2 rows per thread.
@@ -946,23 +965,10 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
       const int N0 = H.ph.N[0], N1 = H.ph.N[1];
       const int clo0 = H.sd.clo[0], chi0 = H.sd.chi[0], clo1 = H.sd.clo[1], chi1 = H.sd.chi[1];
       const bool run = phase == PH_RUN;
+      const T* const wcol = sv + SH * SWp;
+      const T* const ucol = wcol + cr;
+      const T* const lcol = ucol + cr;
 
-      // Per-column tables of the band (after the staged rows in shared
-      // memory): theta weight of owned columns (0 elsewhere), 1 for updated
-      // columns (inside the band, not a transmission column), and the local
-      // trapezoid weight for the L2 increment.
-      const int cr = (cols + 3) & ~3;
-      T* wcol = sv + SH * SWp;
-      T* ucol = wcol + cr;
-      T* lcol = ucol + cr;
-      for (int c = tid; c < cr; c += NT) {
-        const int i = i0 + c, gi = g00 + i;
-        const bool valid = c < cols;
-        wcol[c] = (valid && i >= clo0 && i <= chi0) ? ((gi == 0 || gi == N0 - 1) ? hw0 : h0) : T(0);
-        ucol[c] = (valid && i != dlx && i != dhx) ? T(1) : T(0);
-        lcol[c] = (i == 0 || i == n0 - 1) ? hw0 : h0;
-      }
-      __syncthreads();
       // partial sums: theta, sum of (G - c) over updated nodes (a non-finite
       // value anywhere makes it non-finite), extrema of G - c, min det
       const RunK<T> K = make_runk<T>(H.ph, H.ps, phase);
