@@ -897,6 +897,35 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
         lcol[c] = (i == 0 || i == n0 - 1) ? hw0 : h0;
       }
       }
+      // Transmission nodes of the band (Eq. transmission_condition3): whole
+      // transmission rows, then the transmission columns of the other rows,
+      // one node per thread, while the staging copies are in flight (the
+      // main loop does not store these nodes).
+      if (phase == PH_RUN) {
+        const int jr0 = (dly >= j0 && dly < j0 + rows) ? dly : -1;
+        const int jr1 = (dhy >= j0 && dhy < j0 + rows) ? dhy : -1;
+        const int ic0 = (dlx >= i0 && dlx < i0 + cols) ? dlx : -1;
+        const int ic1 = (dhx >= i0 && dhx < i0 + cols) ? dhx : -1;
+        const int nrw = (jr0 >= 0 ? 1 : 0) + (jr1 >= 0 ? 1 : 0);
+        const int ncl = (ic0 >= 0 ? 1 : 0) + (ic1 >= 0 ? 1 : 0);
+        const int nrow_e = nrw * cols;
+        const int total = nrow_e + ncl * rows;
+        for (int e = tid; e < total; e += NT) {
+          int i, j;
+          if (e < nrow_e) {
+            const int q = e >= cols ? 1 : 0;
+            j = (q == 0 && jr0 >= 0) ? jr0 : jr1;
+            i = i0 + e - q * cols;
+          } else {
+            const int e2 = e - nrow_e;
+            const int q = e2 >= rows ? 1 : 0;
+            i = (q == 0 && ic0 >= 0) ? ic0 : ic1;
+            j = j0 + e2 - q * rows;
+            if (j == jr0 || j == jr1) continue;  // corner: done with its row
+          }
+          st_global(dst + j * pitch + i, gather_owner<T>(a, H, i, j, 0));
+        }
+      }
       // (b) halo columns on the subdomain's x faces (Neumann mirror; clamp on
       //     transmission faces, where the value is never used): loaded now,
       //     written after the copies land.  At most 2 rows per thread.
@@ -982,16 +1011,18 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
         Vec4<T> o;
         stencil_run4<T>(K, H.ph.mon, sv + (r + 1) * SWp + c0 + 4, SWp, wcol + c0, ucol + c0,
                         lcol + c0, rowdir, wyo, wly, fma((T)gj, K.h1, K.lo1), g00 + i0 + c0, o, A);
-        if (run) {
-          if (rowdir || (i0 + c0 <= dlx) || (i0 + c0 + 3 >= dhx && dhx >= 0)) {
+        if (run && !rowdir) {
+          T* const q = dst + j * pitch + i0 + c0;
+          if ((i0 + c0 <= dlx) || (i0 + c0 + 3 >= dhx && dhx >= 0)) {
+            // a run holding a transmission column: updated nodes only
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int i = i0 + c0 + u;
-              if (c0 + u < cols && (rowdir || i == dlx || i == dhx))
-                o.v[u] = gather_owner<T>(a, H, i, j, 0);
+              if (i != dlx && i != dhx) st_global(q + u, o.v[u]);
             }
+          } else {
+            o.stg(q);
           }
-          o.stg(dst + j * pitch + i0 + c0);
         }
       }
       const P2<T> th2 = A.th2, gs2 = A.gs2;
@@ -1858,7 +1889,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
 // ---------------------------------------------------------------- dispatch
 // Compiled shapes.  2D: (threads, band nodes FP32, band nodes FP64); the
 // staged band plus halo is at most 3x the band nodes.  3D: (TX, TY, TZ).
-#define PMA_T2D(X) X(128, 1024, 512) X(256, 2048, 1024) X(256, 1024, 1024) X(512, 3072, 1536)
+#define PMA_T2D(X) X(128, 2048, 1024) X(96, 1536, 768) X(128, 2560, 1280) X(128, 1024, 512)
 // 3D: (threads, nodes per plane box, planes FP32, planes FP64, dynamic
 // shared memory in KiB for the staged box and the column tables).
 #define PMA_T3D(X) X(128, 512, 8, 4, 64) X(128, 512, 16, 8, 96) X(256, 1024, 8, 4, 96)
