@@ -216,10 +216,14 @@ pma_status pma_destroy(pma_ctx *ctx);
  *                          window, transmission values and theta exchanged
  *                          through distributed shared memory; 0 = band
  *                          kernels only (default).  Batched launch mode only;
- *                          decided per request when it is admitted. */
+ *                          decided per request when it is admitted.
+ *   PMA_OPT_TIME_SWEEPS    1 = time every sweep launch with a pair of CUDA
+ *                          events on the context's stream (recorded inside
+ *                          the windows' graphs); sums in pma_stats
+ *                          (sweep_kernel_ms, sweep_kernel_launches). */
 enum { PMA_OPT_WINDOW_STEPS = 1, PMA_OPT_USE_GRAPHS = 2, PMA_OPT_LAUNCH_MODE = 3,
        PMA_OPT_TILE_2D = 4, PMA_OPT_TILE_3D = 5, PMA_OPT_MAX_ACTIVE = 6,
-       PMA_OPT_RESIDENT = 7 };
+       PMA_OPT_RESIDENT = 7, PMA_OPT_TIME_SWEEPS = 8 };
 enum { PMA_LAUNCH_BATCHED = 0, PMA_LAUNCH_PER_SUBDOMAIN = 1 };
 pma_status pma_set_option(pma_ctx *ctx, int32_t option, int64_t value);
 pma_status pma_get_option(pma_ctx *ctx, int32_t option, int64_t *value);
@@ -318,6 +322,8 @@ typedef struct {
   double d2h_bytes;
   int64_t res_launches;
   int64_t res_node_updates;
+  double sweep_kernel_ms;         /* PMA_OPT_TIME_SWEEPS: device time of the sweeps */
+  int64_t sweep_kernel_launches;  /* and the number of timed sweep launches        */
 } pma_stats;
 pma_status pma_get_stats(pma_ctx *ctx, pma_stats *out, int32_t reset);
 

@@ -345,6 +345,13 @@ struct pma_ctx {
   // counters (pma_get_stats)
   pma_stats stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // PMA_OPT_TIME_SWEEPS: a pair of timing events around every sweep launch
+  // (external event records inside the window's graph)
+  int opt_time_sweeps = 0;
+  std::vector<cudaEvent_t> tev;
+  int tev_used = 0;
+  bool capturing = false;
+  int graph_steps_timed = 0;
 
   // server
   std::thread server;
@@ -791,9 +798,19 @@ LaunchArgs args_for(pma_ctx* c, int k, int t0, int n) {
   return a;
 }
 
+pma_status time_mark(pma_ctx* c) {
+  if (!c->opt_time_sweeps || c->tev_used >= (int)c->tev.size()) return PMA_OK;
+  PMA_CK(cudaEventRecordWithFlags(c->tev[c->tev_used++], c->stream,
+                                  c->capturing ? cudaEventRecordExternal
+                                               : cudaEventRecordDefault));
+  return PMA_OK;
+}
+
 pma_status launch_step(pma_ctx* c) {
   for (int k = 0; k < NUM_CLS; ++k) {
     if (c->nwork[k] == 0) continue;
+    pma_status st = time_mark(c);
+    if (st != PMA_OK) return st;
     if (c->launch_mode == PMA_LAUNCH_PER_SUBDOMAIN) {
       for (const SubDesc& sd : c->h_subs) {
         const int n = sd.tile_end - sd.tile_begin;
@@ -805,6 +822,8 @@ pma_status launch_step(pma_ctx* c) {
       LaunchArgs a = args_for(c, k, 0, c->nwork[k]);
       PMA_CK(launch_sweep(k, c->tile_id[k], a, c->stream));
     }
+    st = time_mark(c);
+    if (st != PMA_OK) return st;
     PMA_CK(launch_finish(c->d_fin[k], c->nfin[k], c->d_subs, c->d_probs, c->d_state,
                          c->d_part[k], c->stream));
   }
@@ -838,6 +857,18 @@ pma_status run_window(pma_ctx* c, int steps) {
   const bool graphs = c->use_graphs && c->launch_mode == PMA_LAUNCH_BATCHED;
   const int nres = res_launches(c);
   const int nband = launches_per_step(c);
+  if (c->opt_time_sweeps) {
+    const size_t need = (size_t)2 * NUM_CLS * steps;
+    if (c->tev.size() < need) {
+      while (c->tev.size() < need) {
+        cudaEvent_t e = nullptr;
+        PMA_CK(cudaEventCreate(&e));
+        c->tev.push_back(e);
+      }
+      c->graph_valid = false;
+    }
+  }
+  c->tev_used = 0;
   PMA_CK(cudaEventRecord(c->ev0, c->stream));
   if (nres > 0) {
     pma_status st = launch_res_window(c, steps);
@@ -854,7 +885,10 @@ pma_status run_window(pma_ctx* c, int steps) {
       cudaGraph_t g = nullptr;
       PMA_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
       pma_status st = PMA_OK;
+      c->capturing = true;
       for (int s = 0; s < steps && st == PMA_OK; ++s) st = launch_step(c);
+      c->capturing = false;
+      c->graph_steps_timed = c->tev_used;
       cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
       if (st != PMA_OK) {
         if (g) cudaGraphDestroy(g);
@@ -867,6 +901,7 @@ pma_status run_window(pma_ctx* c, int steps) {
       c->graph_steps = steps;
       c->graph_valid = true;
     }
+    c->tev_used = c->graph_steps_timed;
     PMA_CK(cudaGraphLaunch(c->gexec, c->stream));
   } else {
     for (int s = 0; s < steps; ++s) {
@@ -886,6 +921,12 @@ pma_status run_window(pma_ctx* c, int steps) {
   PMA_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   c->stats.windows += 1;
   c->stats.window_ms += ms;
+  for (int i = 0; i + 1 < c->tev_used; i += 2) {
+    float km = 0.f;
+    PMA_CK(cudaEventElapsedTime(&km, c->tev[i], c->tev[i + 1]));
+    c->stats.sweep_kernel_ms += km;
+    c->stats.sweep_kernel_launches += 1;
+  }
   c->stats.sweep_launches += (int64_t)steps * nband + nres;
   c->stats.res_launches += nres;
   c->stats.d2h_bytes += (double)sizeof(ProbState) * c->slot_cap;
@@ -1142,6 +1183,7 @@ pma_status pma_destroy(pma_ctx* c) {
   cudaFree(c->d_queue);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
   for (int f = 0; f < 2; ++f)
     for (int id = 0; id < kResClasses; ++id) cudaFree(c->rg[f][id].d);
   for (int k = 0; k < 2 * kResClasses; ++k) {
@@ -1184,6 +1226,7 @@ pma_status pma_set_option(pma_ctx* c, int32_t opt, int64_t v) {
       if (v < 0) return PMA_ERR_INVALID;
       c->max_active = (int)v;
       break;
+    case PMA_OPT_TIME_SWEEPS: c->opt_time_sweeps = v ? 1 : 0; break;
     case PMA_OPT_RESIDENT:
       if (v < 0) return PMA_ERR_INVALID;
       c->opt_resident = (int)std::min<int64_t>(v, kResClasses);
@@ -1205,6 +1248,7 @@ pma_status pma_get_option(pma_ctx* c, int32_t opt, int64_t* v) {
     case PMA_OPT_TILE_3D: *v = c->opt_tile3d; break;
     case PMA_OPT_MAX_ACTIVE: *v = c->max_active; break;
     case PMA_OPT_RESIDENT: *v = c->opt_resident; break;
+    case PMA_OPT_TIME_SWEEPS: *v = c->opt_time_sweeps; break;
     default: return PMA_ERR_INVALID;
   }
   return PMA_OK;

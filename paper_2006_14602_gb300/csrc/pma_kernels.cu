@@ -1579,6 +1579,49 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
         }
       }
       cp_async_commit();
+      // Transmission nodes of the box (Eq. transmission_condition3), one
+      // per thread while the staging copies are in flight: whole
+      // transmission planes, then in the other planes the transmission rows
+      // and the transmission columns of the remaining rows.
+      if (phase == PH_RUN) {
+        const int kp0 = (dlz >= k0 && dlz < k0 + depth) ? dlz : -1;
+        const int kp1 = (dhz >= k0 && dhz < k0 + depth) ? dhz : -1;
+        const int jr0 = (dly >= j0 && dly < j0 + rows) ? dly : -1;
+        const int jr1 = (dhy >= j0 && dhy < j0 + rows) ? dhy : -1;
+        const int ic0 = (dlx >= i0 && dlx < i0 + cols) ? dlx : -1;
+        const int ic1 = (dhx >= i0 && dhx < i0 + cols) ? dhx : -1;
+        const int npl = (kp0 >= 0 ? 1 : 0) + (kp1 >= 0 ? 1 : 0);
+        const int nrw = (jr0 >= 0 ? 1 : 0) + (jr1 >= 0 ? 1 : 0);
+        const int ncl = (ic0 >= 0 ? 1 : 0) + (ic1 >= 0 ? 1 : 0);
+        const int plane_e = rows * cols, nrow_e = nrw * cols, per_plane = nrow_e + ncl * rows;
+        const int total = npl * plane_e + depth * per_plane;
+        for (int e = tid; e < total; e += NT) {
+          int i, j, kk;
+          if (e < npl * plane_e) {
+            const int q = e >= plane_e ? 1 : 0, rem = e - q * plane_e;
+            kk = (q == 0 && kp0 >= 0) ? kp0 : kp1;
+            const int rr = rem / cols;
+            j = j0 + rr;
+            i = i0 + rem - rr * cols;
+          } else {
+            const int e2 = e - npl * plane_e, l = e2 / per_plane;
+            kk = k0 + l;
+            if (kk == kp0 || kk == kp1) continue;  // done with its plane
+            const int e3 = e2 - l * per_plane;
+            if (e3 < nrow_e) {
+              const int q = e3 >= cols ? 1 : 0;
+              j = (q == 0 && jr0 >= 0) ? jr0 : jr1;
+              i = i0 + e3 - q * cols;
+            } else {
+              const int e4 = e3 - nrow_e, q = e4 >= rows ? 1 : 0;
+              i = (q == 0 && ic0 >= 0) ? ic0 : ic1;
+              j = j0 + e4 - q * rows;
+              if (j == jr0 || j == jr1) continue;  // corner: done with its row
+            }
+          }
+          st_global(dst + kk * ppitch + j * pitch + i, gather_owner<T>(a, H, i, j, kk));
+        }
+      }
       // (b) x-halo columns (Neumann mirror; clamp on transmission faces)
       const bool left = (i0 == 0), right = (i0 + cols == n0);
       T hl[HMAX], hr[HMAX];
@@ -1820,16 +1863,17 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
               ws += w.y();
             }
           }
-          if (run) {
-            if (rowdir || plndir || (i0 + c0 <= dlx) || (i0 + c0 + 3 >= dhx && dhx >= 0)) {
+          if (run && !rowdir && !plndir) {
+            T* const q = dst + kk * ppitch + j * pitch + i0 + c0;
+            if ((i0 + c0 <= dlx) || (i0 + c0 + 3 >= dhx && dhx >= 0)) {
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
                 const int i = i0 + c0 + u;
-                if (c0 + u < cols && (rowdir || plndir || i == dlx || i == dhx))
-                  o.v[u] = gather_owner<T>(a, H, i, j, kk);
+                if (i != dlx && i != dhx) st_global(q + u, o.v[u]);
               }
+            } else {
+              o.stg(q);
             }
-            o.stg(dst + kk * ppitch + j * pitch + i0 + c0);
           }
         }
       }

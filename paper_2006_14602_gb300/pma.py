@@ -45,6 +45,7 @@ PMA_OPT_TILE_2D = 4
 PMA_OPT_TILE_3D = 5
 PMA_OPT_MAX_ACTIVE = 6
 PMA_OPT_RESIDENT = 7
+PMA_OPT_TIME_SWEEPS = 8
 PMA_LAUNCH_BATCHED = 0
 PMA_LAUNCH_PER_SUBDOMAIN = 1
 
@@ -100,7 +101,8 @@ class pma_stats(C.Structure):
                 ("other_launches", C.c_int64), ("node_updates", C.c_int64),
                 ("sweep_bytes", C.c_double), ("window_ms", C.c_double),
                 ("h2d_bytes", C.c_double), ("d2h_bytes", C.c_double),
-                ("res_launches", C.c_int64), ("res_node_updates", C.c_int64)]
+                ("res_launches", C.c_int64), ("res_node_updates", C.c_int64),
+                ("sweep_kernel_ms", C.c_double), ("sweep_kernel_launches", C.c_int64)]
 
 
 _lib = None
@@ -389,7 +391,7 @@ class Context:
     _OPTS = {"window_steps": PMA_OPT_WINDOW_STEPS, "use_graphs": PMA_OPT_USE_GRAPHS,
              "launch_mode": PMA_OPT_LAUNCH_MODE, "tile_2d": PMA_OPT_TILE_2D,
              "tile_3d": PMA_OPT_TILE_3D, "max_active": PMA_OPT_MAX_ACTIVE,
-             "resident": PMA_OPT_RESIDENT}
+             "resident": PMA_OPT_RESIDENT, "time_sweeps": PMA_OPT_TIME_SWEEPS}
 
     def set(self, name: str, value: int):
         st = pma_set_option(self.h, self._OPTS[name], int(value))

@@ -72,6 +72,17 @@ def test_dd_2d_ragged(prec, n, parts, o, resident):
     _check(prob, resident=resident, window_steps=40)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_subdomains_wider_than_one_band(prec):
+    """Subdomains of about 1150 columns are cut into two strips of bands
+    (at most 1024 columns each): transmission columns, mirror halos and the
+    strip seam all meet in one request."""
+    n = (2300, 40, 1)
+    prob = W.Problem(dim=2, n=n, monitor=W.sine_monitor(), parts=(2, 1, 1), overlap=6,
+                     dt=W.dt_for(n, 2), tol=0.0, max_steps=25, precision=prec)
+    _check(prob, psi=False)
+
+
 @pytest.mark.parametrize("mon", ["sine", "bumps", "product", "burgers"])
 def test_monitor_kinds_2d(mon):
     rng = np.random.default_rng(5)
