@@ -217,10 +217,13 @@ pma_status pma_destroy(pma_ctx *ctx);
  *                          through distributed shared memory; 0 = band
  *                          kernels only (default).  Batched launch mode only;
  *                          decided per request when it is admitted.
- *   PMA_OPT_TIME_SWEEPS    1 = time every sweep launch with a pair of CUDA
- *                          events on the context's stream (recorded inside
- *                          the windows' graphs); sums in pma_stats
- *                          (sweep_kernel_ms, sweep_kernel_launches). */
+ *   PMA_OPT_TIME_SWEEPS    k > 0: time the sweep launches of every k-th step
+ *                          of a window with a pair of CUDA events on the
+ *                          context's stream (recorded inside the windows'
+ *                          graphs; each pair costs about a microsecond, so
+ *                          k = 1 slows a step by several per cent); sums in
+ *                          pma_stats (sweep_kernel_ms, sweep_kernel_launches).
+ *                          0 = off (default). */
 enum { PMA_OPT_WINDOW_STEPS = 1, PMA_OPT_USE_GRAPHS = 2, PMA_OPT_LAUNCH_MODE = 3,
        PMA_OPT_TILE_2D = 4, PMA_OPT_TILE_3D = 5, PMA_OPT_MAX_ACTIVE = 6,
        PMA_OPT_RESIDENT = 7, PMA_OPT_TIME_SWEEPS = 8 };
@@ -302,7 +305,9 @@ pma_status pma_release(pma_ctx *ctx, uint64_t req_id);
 /* Number of requests queued, admitted and finished-but-unreleased. */
 pma_status pma_counts(pma_ctx *ctx, int32_t *queued, int32_t *active, int32_t *finished);
 
-/* Counters of the context since creation or the last reset.  window_ms is
+/* Counters of the context since creation or the last reset.
+ * sweep_launches counts the sweep kernels (band or resident), other_launches
+ * the per-problem finish and the combination kernels.  window_ms is
  * the device time of the stepping windows, measured with CUDA events on
  * the context's stream around the sweep launches only; node_updates counts
  * subdomain nodes advanced by one step; sweep_bytes is the algorithmic HBM

@@ -345,9 +345,11 @@ struct pma_ctx {
   // counters (pma_get_stats)
   pma_stats stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  // PMA_OPT_TIME_SWEEPS: a pair of timing events around every sweep launch
-  // (external event records inside the window's graph)
+  // PMA_OPT_TIME_SWEEPS = k: a pair of timing events around the sweep
+  // launches of every k-th step of a window (external event records inside
+  // the window's graph)
   int opt_time_sweeps = 0;
+  bool time_this_step = false;
   std::vector<cudaEvent_t> tev;
   int tev_used = 0;
   bool capturing = false;
@@ -799,7 +801,7 @@ LaunchArgs args_for(pma_ctx* c, int k, int t0, int n) {
 }
 
 pma_status time_mark(pma_ctx* c) {
-  if (!c->opt_time_sweeps || c->tev_used >= (int)c->tev.size()) return PMA_OK;
+  if (!c->time_this_step || c->tev_used >= (int)c->tev.size()) return PMA_OK;
   PMA_CK(cudaEventRecordWithFlags(c->tev[c->tev_used++], c->stream,
                                   c->capturing ? cudaEventRecordExternal
                                                : cudaEventRecordDefault));
@@ -830,7 +832,9 @@ pma_status launch_step(pma_ctx* c) {
   return PMA_OK;
 }
 
-int launches_per_step(pma_ctx* c) {
+// Sweep launches per step (one per class, or one per subdomain in the
+// per-subdomain mode) and finish launches per step (one per class).
+int sweeps_per_step(pma_ctx* c) {
   int n = 0;
   for (int k = 0; k < NUM_CLS; ++k) {
     if (c->nwork[k] == 0) continue;
@@ -840,10 +844,15 @@ int launches_per_step(pma_ctx* c) {
     } else {
       ++n;
     }
-    ++n;  // finish
   }
   return n;
 }
+int finishes_per_step(pma_ctx* c) {
+  int n = 0;
+  for (int k = 0; k < NUM_CLS; ++k) n += c->nwork[k] > 0 ? 1 : 0;
+  return n;
+}
+int launches_per_step(pma_ctx* c) { return sweeps_per_step(c) + finishes_per_step(c); }
 
 pma_status run_window(pma_ctx* c, int steps) {
   if (c->dirty) {
@@ -886,8 +895,12 @@ pma_status run_window(pma_ctx* c, int steps) {
       PMA_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
       pma_status st = PMA_OK;
       c->capturing = true;
-      for (int s = 0; s < steps && st == PMA_OK; ++s) st = launch_step(c);
+      for (int s = 0; s < steps && st == PMA_OK; ++s) {
+        c->time_this_step = c->opt_time_sweeps > 0 && (s % c->opt_time_sweeps) == 0;
+        st = launch_step(c);
+      }
       c->capturing = false;
+      c->time_this_step = false;
       c->graph_steps_timed = c->tev_used;
       cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
       if (st != PMA_OK) {
@@ -905,7 +918,9 @@ pma_status run_window(pma_ctx* c, int steps) {
     PMA_CK(cudaGraphLaunch(c->gexec, c->stream));
   } else {
     for (int s = 0; s < steps; ++s) {
+      c->time_this_step = c->opt_time_sweeps > 0 && (s % c->opt_time_sweeps) == 0;
       pma_status st = launch_step(c);
+      c->time_this_step = false;
       if (st != PMA_OK) return st;
     }
   }
@@ -927,7 +942,8 @@ pma_status run_window(pma_ctx* c, int steps) {
     c->stats.sweep_kernel_ms += km;
     c->stats.sweep_kernel_launches += 1;
   }
-  c->stats.sweep_launches += (int64_t)steps * nband + nres;
+  c->stats.sweep_launches += (int64_t)steps * sweeps_per_step(c) + nres;
+  c->stats.other_launches += (int64_t)steps * finishes_per_step(c);
   c->stats.res_launches += nres;
   c->stats.d2h_bytes += (double)sizeof(ProbState) * c->slot_cap;
   return PMA_OK;
@@ -1226,7 +1242,10 @@ pma_status pma_set_option(pma_ctx* c, int32_t opt, int64_t v) {
       if (v < 0) return PMA_ERR_INVALID;
       c->max_active = (int)v;
       break;
-    case PMA_OPT_TIME_SWEEPS: c->opt_time_sweeps = v ? 1 : 0; break;
+    case PMA_OPT_TIME_SWEEPS:
+      if (v < 0) return PMA_ERR_INVALID;
+      c->opt_time_sweeps = (int)std::min<int64_t>(v, 1 << 20);
+      break;
     case PMA_OPT_RESIDENT:
       if (v < 0) return PMA_ERR_INVALID;
       c->opt_resident = (int)std::min<int64_t>(v, kResClasses);
