@@ -72,7 +72,8 @@ def serving(args):
 
     def run(stream, precision, plain, budget=120 << 30):
         reqs = [(t, p.replace(precision=precision)) for t, p in stream]
-        opts = {"window_steps": args.window, "resident": args.resident}
+        opts = {"window_steps": args.window, "resident": args.resident,
+                "resident_steps": args.resident_steps}
         if plain:
             opts.update(launch_mode=pma.PMA_LAUNCH_PER_SUBDOMAIN, use_graphs=0)
         with pma.Context(0, budget, **opts) as ctx:
@@ -97,8 +98,9 @@ def serving(args):
             wall = time.perf_counter() - t0
             pma.pma_serve_stop(ctx.h)
         return {"meshes_per_s": len(reqs) / wall, "node_updates_per_s": nu / wall,
-                "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99),
-                "wall_s": wall, "requests": len(reqs)}
+                "p10_ms": percentile(lat, 0.1), "p25_ms": percentile(lat, 0.25),
+                "p50_ms": percentile(lat, 0.5), "p90_ms": percentile(lat, 0.9),
+                "p99_ms": percentile(lat, 0.99), "wall_s": wall, "requests": len(reqs)}
 
     def stream_at(rate):
         return W.config5_stream(count=args.requests, rate_hz=rate,
@@ -128,7 +130,8 @@ def serving(args):
                                "%d steps; value = all submitted at once"
                                % (args.requests, args.max2d, args.max3d, args.max_steps or 2000),
                    "requests": args.requests},
-        "latency_ms": {"p50": sat["p50_ms"], "p99": sat["p99_ms"]},
+        "latency_ms": {"p10": sat["p10_ms"], "p25": sat["p25_ms"], "p50": sat["p50_ms"],
+                       "p90": sat["p90_ms"], "p99": sat["p99_ms"]},
         "node_updates_per_s": sat["node_updates_per_s"],
         "poisson_sweep": sweep,
         "small_budget": small,
@@ -484,6 +487,8 @@ def main():
                          "first k shared-memory classes (0: band kernels only)")
     ap.add_argument("--rate", type=float, default=None,
                     help="c5: one Poisson rate (default: 0.25x..1.5x the saturation throughput)")
+    ap.add_argument("--resident-steps", type=int, default=0,
+                    help="steps a resident launch takes per window (0: the window's)")
     ap.add_argument("--budget-mb", type=int, default=16,
                     help="c5: memory budget of the back-pressure run")
     ap.add_argument("--requests", type=int, default=64, help="c5: requests in the stream")

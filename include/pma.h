@@ -223,10 +223,16 @@ pma_status pma_destroy(pma_ctx *ctx);
  *                          graphs; each pair costs about a microsecond, so
  *                          k = 1 slows a step by several per cent); sums in
  *                          pma_stats (sweep_kernel_ms, sweep_kernel_launches).
- *                          0 = off (default). */
+ *                          0 = off (default).
+ *   PMA_OPT_RESIDENT_STEPS steps a resident launch takes per window (0 = the
+ *                          window's steps, default).  A resident step costs
+ *                          a few microseconds against tens for a band step,
+ *                          so resident requests can run several band windows'
+ *                          worth of steps while the band work of a window
+ *                          runs beside them (results do not depend on it). */
 enum { PMA_OPT_WINDOW_STEPS = 1, PMA_OPT_USE_GRAPHS = 2, PMA_OPT_LAUNCH_MODE = 3,
        PMA_OPT_TILE_2D = 4, PMA_OPT_TILE_3D = 5, PMA_OPT_MAX_ACTIVE = 6,
-       PMA_OPT_RESIDENT = 7, PMA_OPT_TIME_SWEEPS = 8 };
+       PMA_OPT_RESIDENT = 7, PMA_OPT_TIME_SWEEPS = 8, PMA_OPT_RESIDENT_STEPS = 9 };
 enum { PMA_LAUNCH_BATCHED = 0, PMA_LAUNCH_PER_SUBDOMAIN = 1 };
 pma_status pma_set_option(pma_ctx *ctx, int32_t option, int64_t value);
 pma_status pma_get_option(pma_ctx *ctx, int32_t option, int64_t *value);

@@ -341,6 +341,7 @@ struct pma_ctx {
   int opt_tile2d = 0, opt_tile3d = 0;
   int max_active = 0;
   int opt_resident = 0;
+  int opt_res_steps = 0;  // steps of a resident launch per window (0: the window's)
 
   // counters (pma_get_stats)
   pma_stats stats{};
@@ -768,7 +769,7 @@ pma_status launch_res_window(pma_ctx* c, int steps) {
       a.subs = c->d_subs;
       a.probs = c->d_probs;
       a.st = c->d_state;
-      a.iters = steps;
+      a.iters = c->opt_res_steps > 0 ? c->opt_res_steps : steps;
       a.pad = 0;
       PMA_CK(launch_res2d(f == 1, id, a, g.nclusters, c->res_csize[f][id], g.smem, ss));
       PMA_CK(cudaEventRecord(c->ev_join[f * kResClasses + id], ss));
@@ -1242,6 +1243,10 @@ pma_status pma_set_option(pma_ctx* c, int32_t opt, int64_t v) {
       if (v < 0) return PMA_ERR_INVALID;
       c->max_active = (int)v;
       break;
+    case PMA_OPT_RESIDENT_STEPS:
+      if (v < 0 || v > (1 << 20)) return PMA_ERR_INVALID;
+      c->opt_res_steps = (int)v;
+      break;
     case PMA_OPT_TIME_SWEEPS:
       if (v < 0) return PMA_ERR_INVALID;
       c->opt_time_sweeps = (int)std::min<int64_t>(v, 1 << 20);
@@ -1268,6 +1273,7 @@ pma_status pma_get_option(pma_ctx* c, int32_t opt, int64_t* v) {
     case PMA_OPT_MAX_ACTIVE: *v = c->max_active; break;
     case PMA_OPT_RESIDENT: *v = c->opt_resident; break;
     case PMA_OPT_TIME_SWEEPS: *v = c->opt_time_sweeps; break;
+    case PMA_OPT_RESIDENT_STEPS: *v = c->opt_res_steps; break;
     default: return PMA_ERR_INVALID;
   }
   return PMA_OK;

@@ -56,15 +56,6 @@ __device__ __forceinline__ const ProbHot<double>* hot_table<double>(const Launch
   return a.hotd;
 }
 
-template <typename T, int NT>
-__device__ __forceinline__ void load_hdr(const LaunchArgs& a, SmemHdr<T>& S) {
-  // S.w was set by thread 0 and published by a __syncthreads()
-  constexpr int C_SD = (int)(sizeof(SubDesc) / 16), C_PS = (int)(sizeof(ProbState) / 16);
-  coop_copy<NT>(&S.sd, a.subs + S.w.sub, sizeof(SubDesc), 0);
-  coop_copy<NT>(&S.ps, a.st + S.w.prob, sizeof(ProbState), C_SD);
-  coop_copy<NT>(&S.ph, hot_table<T>(a) + S.w.prob, sizeof(ProbHot<T>), C_SD + C_PS);
-}
-
 // q = e / d for 0 <= e < 2^24, 1 <= d < 2^16, via an FP32 reciprocal; the
 // estimate is within one of the quotient and the fix-up makes it exact.
 __device__ __forceinline__ int qdiv(int e, int d, float inv_d) {
@@ -387,64 +378,6 @@ __device__ void stage_alternating(const LaunchArgs& a, const SmemHdr<T>& S, T* s
   }
 }
 
-template <typename T>
-__device__ __forceinline__ T init_value(const SmemHdr<T>& S, const double* psi0, int gi, int gj,
-                                        int gl) {
-  if (!psi0) return T(0);
-  const long long gflat =
-      (long long)gi + (long long)S.ph.N[0] * (gj + (long long)S.ph.N[1] * gl);
-  double q = 0.0;
-  const int g[3] = {gi, gj, gl};
-  for (int a = 0; a < 3; ++a)
-    if (a < S.ph.dim) {
-      double xi = (double)S.ph.lo[a] + (double)g[a] * S.ph.hd[a];
-      q += 0.5 * xi * xi;
-    }
-  return (T)(psi0[gflat] - q);
-}
-
-// Right-hand side at one node.  The theta^0 pass only needs rho det and a
-// finiteness check, so it uses the log form whatever the right-hand side.
-template <typename T>
-__device__ __forceinline__ T rhs_value(const SmemHdr<T>& S, int phase, T scale_root, T x0, T x1,
-                                       T x2, T D, T& rho) {
-  rho = rho_at<T>(S.ph.mon, x0, x1, x2);
-  if (S.ph.rhs == PMA_RHS_LOG || phase != PH_RUN) return Fm<T>::ln(rho * D);
-  const T e = T(1) / (T)S.ph.dim;
-  return Fm<T>::pw(scale_root * rho * D, e) - T(1);
-}
-
-template <typename T>
-__device__ __forceinline__ T trap_t(int gi, int N, T h, T hw) {
-  return (gi == 0 || gi == N - 1) ? hw : h;
-}
-
-template <typename T>
-__device__ __forceinline__ void accumulate(const SmemHdr<T>& S, T G, T D, T rho, bool owned,
-                                           int gi, int gj, int gl, int i, int j, int l, T c_lag,
-                                           T& th, T& l2a, T& l2b, T& ws, Acc<T>& acc) {
-  if (!(G == G) || !isfinite(G)) acc.nf += 1;
-  acc.gmax = fmax(acc.gmax, G);
-  acc.gmin = fmin(acc.gmin, G);
-  acc.dmin = fmin(acc.dmin, D);
-  const int dim = S.ph.dim;
-  if (owned) {
-    T w = trap_t<T>(gi, S.ph.N[0], S.ph.h[0], S.ph.hw[0]) *
-          trap_t<T>(gj, S.ph.N[1], S.ph.h[1], S.ph.hw[1]);
-    if (dim > 2) w *= trap_t<T>(gl, S.ph.N[2], S.ph.h[2], S.ph.hw[2]);
-    th = fma(w, rho * D, th);
-  }
-  if (S.ph.stop_norm == PMA_STOP_L2_INCREMENT) {
-    T w = trap_t<T>(i, S.sd.n[0], S.ph.h[0], S.ph.hw[0]) *
-          trap_t<T>(j, S.sd.n[1], S.ph.h[1], S.ph.hw[1]);
-    if (dim > 2) w *= trap_t<T>(l, S.sd.n[2], S.ph.h[2], S.ph.hw[2]);
-    T d = G - c_lag;
-    l2a += w * d * d;
-    l2b += w * d;
-    ws += w;
-  }
-}
-
 // ---------------------------------------------------------------- work queue
 // Persistent CTAs pull work items from a per-launch counter; the last CTA
 // to run out resets the counters for the next launch.  The partial record
@@ -537,12 +470,6 @@ __device__ __forceinline__ P2<double> psub(P2<double> a, P2<double> b) { return 
 template <typename T>
 __device__ __forceinline__ P2<T> pexw(P2<T> a) {
   return P2<T>::mk(Fm<T>::exw(a.x()), Fm<T>::exw(a.y()));
-}
-
-// 16-byte chunk copy global -> shared (VW elements of T).
-template <typename T>
-__device__ __forceinline__ void copy16(T* d, const T* s) {
-  *(int4*)d = __ldcg((const int4*)s);
 }
 
 // ---------------------------------------------------------------- 2D stencil

@@ -46,6 +46,7 @@ PMA_OPT_TILE_3D = 5
 PMA_OPT_MAX_ACTIVE = 6
 PMA_OPT_RESIDENT = 7
 PMA_OPT_TIME_SWEEPS = 8
+PMA_OPT_RESIDENT_STEPS = 9
 PMA_LAUNCH_BATCHED = 0
 PMA_LAUNCH_PER_SUBDOMAIN = 1
 
@@ -391,7 +392,8 @@ class Context:
     _OPTS = {"window_steps": PMA_OPT_WINDOW_STEPS, "use_graphs": PMA_OPT_USE_GRAPHS,
              "launch_mode": PMA_OPT_LAUNCH_MODE, "tile_2d": PMA_OPT_TILE_2D,
              "tile_3d": PMA_OPT_TILE_3D, "max_active": PMA_OPT_MAX_ACTIVE,
-             "resident": PMA_OPT_RESIDENT, "time_sweeps": PMA_OPT_TIME_SWEEPS}
+             "resident": PMA_OPT_RESIDENT, "time_sweeps": PMA_OPT_TIME_SWEEPS,
+             "resident_steps": PMA_OPT_RESIDENT_STEPS}
 
     def set(self, name: str, value: int):
         st = pma_set_option(self.h, self._OPTS[name], int(value))

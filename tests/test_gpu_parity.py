@@ -250,7 +250,8 @@ def test_launch_modes_are_bitwise_identical():
     # the resident path does not depend on the window either
     r1 = pma.solve(prob, window_steps=32, resident=4)[0]
     r2 = pma.solve(prob, window_steps=3, resident=4)[0]
-    assert np.array_equal(r1, r2)
+    r3 = pma.solve(prob, window_steps=8, resident=4, resident_steps=50)[0]
+    assert np.array_equal(r1, r2) and np.array_equal(r1, r3)
     # another tile shape, or the resident path, changes the summation order
     # of theta (a uniform offset of v), so positions agree to rounding
     ref = oracle.solve(prob)
