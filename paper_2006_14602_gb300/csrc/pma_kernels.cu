@@ -555,6 +555,22 @@ struct RunAcc {
 // det D_h^2 Psi, rho(x) and G - c_lag, and returns v + dt (G - c_lag) in o
 // (0 at nodes that are not updated: wc/uc/lc are the run's entries of the
 // column tables, rowdir marks a transmission row).
+// Columns c0-1 .. c0+4 of one staged row (p: column c0 of the row).
+template <typename T>
+__device__ __forceinline__ void load_row6(const T* p, T* w) {
+  Vec4<T> m;
+  w[0] = p[-1];
+  m.lds(p);
+  w[1] = m.v[0]; w[2] = m.v[1]; w[3] = m.v[2]; w[4] = m.v[3];
+  w[5] = p[4];
+}
+
+template <typename T>
+__device__ __forceinline__ void stencil_core4(const RunK<T>& K, const MonT<T>& mon, const T* wS,
+                                              const T* wC, const T* wN, const T* wcp,
+                                              const T* ucp, const T* lcp, bool rowdir, T wyo,
+                                              T wly, T xi1, int gi0, Vec4<T>& o, RunAcc<T>& A);
+
 template <typename T>
 __device__ __forceinline__ void stencil_run4(const RunK<T>& K, const MonT<T>& mon, const T* p,
                                              int SWp, const T* wcp, const T* ucp, const T* lcp,
@@ -562,21 +578,19 @@ __device__ __forceinline__ void stencil_run4(const RunK<T>& K, const MonT<T>& mo
                                              Vec4<T>& o, RunAcc<T>& A) {
   // 3 x 6 window: columns c0-1 .. c0+4 of rows j-1, j, j+1
   T wS[6], wC[6], wN[6];
-  {
-    Vec4<T> m;
-    wS[0] = p[-SWp - 1];
-    m.lds(p - SWp);
-    wS[1] = m.v[0]; wS[2] = m.v[1]; wS[3] = m.v[2]; wS[4] = m.v[3];
-    wS[5] = p[-SWp + 4];
-    wC[0] = p[-1];
-    m.lds(p);
-    wC[1] = m.v[0]; wC[2] = m.v[1]; wC[3] = m.v[2]; wC[4] = m.v[3];
-    wC[5] = p[4];
-    wN[0] = p[SWp - 1];
-    m.lds(p + SWp);
-    wN[1] = m.v[0]; wN[2] = m.v[1]; wN[3] = m.v[2]; wN[4] = m.v[3];
-    wN[5] = p[SWp + 4];
-  }
+  load_row6<T>(p - SWp, wS);
+  load_row6<T>(p, wC);
+  load_row6<T>(p + SWp, wN);
+  stencil_core4<T>(K, mon, wS, wC, wN, wcp, ucp, lcp, rowdir, wyo, wly, xi1, gi0, o, A);
+}
+
+// The stencil, monitor, update and reductions of one run from its 3 x 6
+// window (rows j-1, j, j+1).
+template <typename T>
+__device__ __forceinline__ void stencil_core4(const RunK<T>& K, const MonT<T>& mon, const T* wS,
+                                              const T* wC, const T* wN, const T* wcp,
+                                              const T* ucp, const T* lcp, bool rowdir, T wyo,
+                                              T wly, T xi1, int gi0, Vec4<T>& o, RunAcc<T>& A) {
   Vec4<T> wc, uc;
   wc.lds(wcp);
   uc.lds(ucp);

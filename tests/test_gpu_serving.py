@@ -110,3 +110,19 @@ def test_wait_timeout_and_poll():
         st, done = pma.pma_poll(ctx.h, rid)
         assert st == pma.PMA_OK and done == 1
         assert pma.pma_serve_stop(ctx.h) == pma.PMA_OK
+
+
+def test_sweep_timing_and_launch_counters():
+    """PMA_OPT_TIME_SWEEPS=k times the sweep launch of every k-th step: the
+    timed launches are counted, their device time is positive and below the
+    windows' time, and sweep and finish launches are counted apart."""
+    prob = W.small_case(2, 40, parts=(2, 2, 1), overlap=4, steps=64, precision="fp32")
+    with pma.Context(0, window_steps=16, time_sweeps=4) as ctx:
+        ctx.submit(prob)
+        ctx.run()
+        _, s = pma.pma_get_stats(ctx.h)
+    # INIT_V, INIT_THETA and 64 steps: 66 sweep launches in 5 windows of 16
+    assert s.sweep_launches == s.windows * 16
+    assert s.sweep_kernel_launches == s.windows * 4
+    assert 0 < s.sweep_kernel_ms < s.window_ms
+    assert s.other_launches >= s.windows * 16  # one finish per sweep, plus the combine
