@@ -493,6 +493,9 @@ void fill_hot(const Request& r, const ProbDesc& pd, ProbHot<T>& h) {
   }
   h.mon.base = (T)r.m.base;
   h.mon.p0 = (T)r.m.p0;
+  h.mon_fast = r.m.kind == PMA_MON_SUM ? 1 : 0;
+  for (int t = 0; t < r.m.nterms && t < kMaxTerms; ++t)
+    if (r.m.term[t].type != PMA_TERM_BUMP && r.m.term[t].type != PMA_TERM_RING) h.mon_fast = 0;
   for (int t = 0; t < kMaxTerms; ++t) {
     const pma_term& q = r.m.term[t];
     auto& o = h.mon.t[t];
@@ -521,6 +524,34 @@ int pick_tile(pma_ctx* c, int cls) {
 //   2D: bands of full-width rows (strips of at most t2.cols columns), sized
 //       so that the staged band, its halo and the column tables fit;
 //   3D: boxes of cols x rows nodes per plane over tz planes.
+// Mirror of a node index across a physical face, clamp across a
+// transmission face (the staged halo of a band).
+static int reflect_host(int i, int n, bool phys_lo, bool phys_hi) {
+  if (i < 0) i = phys_lo ? -i : 0;
+  if (i >= n) i = phys_hi ? 2 * (n - 1) - i : n - 1;
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Transmission rows / columns of a staged 2D band (WorkItem::flags).
+static int band_flags(const HostSub& hs, int i0, int j0, int cols, int rows) {
+  const int n0 = hs.n[0], n1 = hs.n[1], f = hs.faces;
+  const bool plx = f & 1, phx = f & 2, ply = f & 4, phy = f & 8;
+  const int dly = ply ? -1 : 0, dhy = phy ? -1 : n1 - 1;
+  const int sh = rows + 2;
+  const int cand[4] = {0, 1, sh - 2, sh - 1};
+  int fl = 0;
+  for (int q = 0; q < 4; ++q) {
+    bool dup = false;
+    for (int p = 0; p < q; ++p) dup = dup || cand[p] == cand[q];
+    if (dup) continue;
+    const int jj = reflect_host(j0 - 1 + cand[q], n1, ply, phy);
+    if (jj == dly || jj == dhy) fl |= 1 << q;
+  }
+  if (!plx && i0 == 0) fl |= 16;
+  if (!phx && i0 + cols == n0) fl |= 32;
+  return fl;
+}
+
 void push_items(const HostSub& hs, int dim, bool fp64, int tile_id, int sidx, int slot,
                 std::vector<WorkItem>& wl) {
   if (dim == 2) {
@@ -530,11 +561,12 @@ void push_items(const HostSub& hs, int dim, bool fp64, int tile_id, int sidx, in
       const int cr = (cols + 3) & ~3;
       const int swp = cr + 8;
       int rows = std::max(1, std::min(hs.n[1], t2.nodes / cr));
-      while (rows > 1 && ((rows + 2) * swp + 3 * cr > t2.smax || rows + 2 > 2 * t2.threads))
+      while (rows > 1 && ((rows + 2) * swp + 5 * cr > t2.smax || rows + 2 > 2 * t2.threads))
         --rows;
       for (int y = 0; y < hs.n[1]; y += rows) {
         const int rr = std::min(rows, hs.n[1] - y);
-        wl.push_back(WorkItem{sidx, slot, x | (y << 16), cols | (rr << 16), 0, {0, 0, 0}});
+        wl.push_back(WorkItem{sidx, slot, x | (y << 16), cols | (rr << 16), 0,
+                              band_flags(hs, x, y, cols, rr), {0, 0}});
       }
     }
   } else {
@@ -551,8 +583,8 @@ void push_items(const HostSub& hs, int dim, bool fp64, int tile_id, int sidx, in
         const int rr = std::min(rows, hs.n[1] - y);
         for (int z = 0; z < hs.n[2]; z += t3.tz) {
           const int d = std::min(t3.tz, hs.n[2] - z);
-          wl.push_back(WorkItem{sidx, slot, x | (y << 16), cols | (rr << 16), z | (d << 16),
-                                {0, 0, 0}});
+          wl.push_back(WorkItem{sidx, slot, x | (y << 16), cols | (rr << 16), z | (d << 16), 0,
+                                {0, 0}});
         }
       }
     }

@@ -64,7 +64,9 @@ struct alignas(16) ProbHot {
   int dim, rhs, normalize, stop_norm;
   int N[3], sub_base;
   int parts[3], ntiles;
-  int alternating, pad1[3];  // 1: alternating transmission (Algorithm 1)
+  int alternating;  // 1: alternating transmission (Algorithm 1)
+  int mon_fast;     // 1: sum of bump / ring terms (the packed monitor path)
+  int pad1[2];
   T lo[3], h[3], inv2h[3], invh2[3], inv4hh[3], hw[3];
   T dt, vol;
   double hd[3];
@@ -130,7 +132,12 @@ struct alignas(16) WorkItem {
   int ij;    // i0 | j0 << 16
   int ext;   // cols | rows << 16
   int kz;    // 3D: k0 | depth << 16 (planes); 2D: 0
-  int pad[3];
+  // 2D: transmission rows and columns of the staged band (halo included):
+  // bit q (q < 4) = staged row {0, 1, rows, rows + 1}[q] is a transmission
+  // row (each row flagged once); bit 4 / 5 = staged column 4 / cols + 3
+  // (local column 0 / n0 - 1) is a transmission column.  3D: 0.
+  int flags;
+  int pad[2];
 };
 
 struct Partial {

@@ -91,17 +91,27 @@ __device__ __forceinline__ T warp_min(T v) {
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+// FP32 extrema of a warp in one instruction (redux.sync, sm_100 family);
+// NaN lanes are ignored, as by fmaxf / fminf.
+template <>
+__device__ __forceinline__ float warp_max<float>(float v) {
+  float r;
+  asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
+}
+template <>
+__device__ __forceinline__ float warp_min<float>(float v) {
+  float r;
+  asm("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
+}
 template <typename T>
 __device__ __forceinline__ T big_val();
 template <>
 __device__ __forceinline__ float big_val<float>() { return FLT_MAX; }
 template <>
 __device__ __forceinline__ double big_val<double>() { return DBL_MAX; }
-__device__ __forceinline__ int warp_isum(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
+__device__ __forceinline__ int warp_isum(int v) { return __reduce_add_sync(0xffffffffu, v); }
 
 // Reduce the tile's accumulators (in the sweep precision, fixed order) and
 // write the tile's partial record.
@@ -501,8 +511,12 @@ template <typename T>
 __device__ __forceinline__ RunK<T> make_runk(const ProbHot<T>& ph, const ProbState& ps, int phase) {
   RunK<T> K;
   K.c_lag = (T)ps.c_lag;
-  K.scale_root = (T)(ph.vol / (T)ps.theta_prev);
-  K.inv_dim = T(1) / (T)ph.dim;
+  K.logrhs = ph.rhs == PMA_RHS_LOG || phase != PH_RUN;
+  K.scale_root = K.inv_dim = T(0);
+  if (!K.logrhs) {
+    K.scale_root = (T)(ph.vol / (T)ps.theta_prev);
+    K.inv_dim = T(1) / (T)ph.dim;
+  }
   K.lo0 = ph.lo[0];
   K.lo1 = ph.lo[1];
   K.h0 = ph.h[0];
@@ -520,32 +534,59 @@ __device__ __forceinline__ RunK<T> make_runk(const ProbHot<T>& ph, const ProbSta
   K.BIG = P2<T>::s(big_val<T>());
   K.NBIG = P2<T>::s(-big_val<T>());
   K.want_l2 = ph.stop_norm == PMA_STOP_L2_INCREMENT;
-  K.logrhs = ph.rhs == PMA_RHS_LOG || phase != PH_RUN;
   K.nterms = ph.mon.nterms;
-  bool fast = (ph.mon.kind == PMA_MON_SUM);
-  for (int q = 0; q < kMaxTerms; ++q)
-    if (q < K.nterms && ph.mon.t[q].type != PMA_TERM_BUMP && ph.mon.t[q].type != PMA_TERM_RING)
-      fast = false;
-  K.fast = fast;
+  K.fast = ph.mon_fast != 0;
   return K;
 }
 
+// G - c_lag of one node from rho det (the update's right-hand side: Eq.
+// pmae in log form, or the d-th root form), the same arithmetic per lane as
+// the packed evaluation in the stencil.
+template <typename T>
+__device__ __forceinline__ P2<T> rhs_pair(const RunK<T>& K, P2<T> rD);
+template <>
+__device__ __forceinline__ P2<float> rhs_pair<float>(const RunK<float>& K, P2<float> rD) {
+  if (K.logrhs)
+    return pfma(P2<float>::mk(lg2_approx(rD.x()), lg2_approx(rD.y())), P2<float>::s(Fm<float>::kLn2),
+                K.NCL);
+  return P2<float>::mk(Fm<float>::pw(K.scale_root * rD.x(), K.inv_dim) - 1.0f - K.c_lag,
+                       Fm<float>::pw(K.scale_root * rD.y(), K.inv_dim) - 1.0f - K.c_lag);
+}
+template <>
+__device__ __forceinline__ P2<double> rhs_pair<double>(const RunK<double>& K, P2<double> rD) {
+  if (K.logrhs) return padd(P2<double>::mk(log(rD.x()), log(rD.y())), K.NCL);
+  return P2<double>::mk(pow(K.scale_root * rD.x(), K.inv_dim) - 1.0 - K.c_lag,
+                        pow(K.scale_root * rD.y(), K.inv_dim) - 1.0 - K.c_lag);
+}
+
 // Partial sums of one thread: theta (owned nodes), sum of G - c over updated
-// nodes (a non-finite value anywhere makes it non-finite), extrema of G - c,
-// min det, and the L2-increment pieces.
+// nodes (a non-finite value anywhere makes it non-finite), extrema of
+// rho det over updated nodes (G - c is monotone in it, so the extrema of
+// G - c follow from two evaluations per thread), min det, and the
+// L2-increment pieces.
 template <typename T>
 struct RunAcc {
   P2<T> th2, gs2;
-  T gcmax, gcmin, dmin, l2a, l2b, ws;
+  T rmax, rmin, dmin, l2a, l2b, ws;
   __device__ __forceinline__ static RunAcc zero() {
     RunAcc a;
     a.th2 = P2<T>::s(T(0));
     a.gs2 = P2<T>::s(T(0));
-    a.gcmax = -big_val<T>();
-    a.gcmin = big_val<T>();
+    a.rmax = T(0);
+    a.rmin = big_val<T>();
     a.dmin = big_val<T>();
     a.l2a = a.l2b = a.ws = T(0);
     return a;
+  }
+  // extrema of G (= G - c_lag + c_lag), min det and the non-finite flag of
+  // the thread's nodes; a thread without updated nodes (or whose largest
+  // rho det is not positive: tangled) keeps the neutral extrema
+  __device__ __forceinline__ void fold(const RunK<T>& K, Acc<T>& acc) const {
+    const P2<T> g = rhs_pair<T>(K, P2<T>::mk(rmax > T(0) ? rmax : T(1), rmin));
+    if (rmax > T(0)) acc.gmax = g.x() + K.c_lag;
+    if (rmin < big_val<T>()) acc.gmin = g.y() + K.c_lag;
+    acc.dmin = dmin;
+    if (!isfinite(gs2.x() + gs2.y())) acc.nf += 1;
   }
 };
 
@@ -565,35 +606,46 @@ __device__ __forceinline__ void load_row6(const T* p, T* w) {
   w[5] = p[4];
 }
 
+// Column tables of a staged band or subdomain, at the run's first column:
+// theta weight (owned columns, else 0), 1 at updated columns (else 0), the
+// local trapezoid weight, and with TAB the node's xi_x and +big at columns
+// that are not updated (else 0); without TAB those two are formed from the
+// global column index gi0.
 template <typename T>
-__device__ __forceinline__ void stencil_core4(const RunK<T>& K, const MonT<T>& mon, const T* wS,
-                                              const T* wC, const T* wN, const T* wcp,
-                                              const T* ucp, const T* lcp, bool rowdir, T wyo,
-                                              T wly, T xi1, int gi0, Vec4<T>& o, RunAcc<T>& A);
+struct ColTab {
+  const T *w, *u, *l, *x, *k;
+  int gi0;
+};
 
-template <typename T>
+template <typename T, bool TAB>
+__device__ __forceinline__ void stencil_core4(const RunK<T>& K, const MonT<T>& mon, const T* wS,
+                                              const T* wC, const T* wN, const ColTab<T>& ct,
+                                              bool rowdir, T wyo, T wly, T xi1, Vec4<T>& o,
+                                              RunAcc<T>& A);
+
+template <typename T, bool TAB>
 __device__ __forceinline__ void stencil_run4(const RunK<T>& K, const MonT<T>& mon, const T* p,
-                                             int SWp, const T* wcp, const T* ucp, const T* lcp,
-                                             bool rowdir, T wyo, T wly, T xi1, int gi0,
-                                             Vec4<T>& o, RunAcc<T>& A) {
+                                             int SWp, const ColTab<T>& ct, bool rowdir, T wyo,
+                                             T wly, T xi1, Vec4<T>& o, RunAcc<T>& A) {
   // 3 x 6 window: columns c0-1 .. c0+4 of rows j-1, j, j+1
   T wS[6], wC[6], wN[6];
   load_row6<T>(p - SWp, wS);
   load_row6<T>(p, wC);
   load_row6<T>(p + SWp, wN);
-  stencil_core4<T>(K, mon, wS, wC, wN, wcp, ucp, lcp, rowdir, wyo, wly, xi1, gi0, o, A);
+  stencil_core4<T, TAB>(K, mon, wS, wC, wN, ct, rowdir, wyo, wly, xi1, o, A);
 }
 
 // The stencil, monitor, update and reductions of one run from its 3 x 6
 // window (rows j-1, j, j+1).
-template <typename T>
+template <typename T, bool TAB>
 __device__ __forceinline__ void stencil_core4(const RunK<T>& K, const MonT<T>& mon, const T* wS,
-                                              const T* wC, const T* wN, const T* wcp,
-                                              const T* ucp, const T* lcp, bool rowdir, T wyo,
-                                              T wly, T xi1, int gi0, Vec4<T>& o, RunAcc<T>& A) {
-  Vec4<T> wc, uc;
-  wc.lds(wcp);
-  uc.lds(ucp);
+                                              const T* wC, const T* wN, const ColTab<T>& ct,
+                                              bool rowdir, T wyo, T wly, T xi1, Vec4<T>& o,
+                                              RunAcc<T>& A) {
+  Vec4<T> wc, uc, xc;
+  wc.lds(ct.w);
+  uc.lds(ct.u);
+  if (TAB) xc.lds(ct.x);
   const P2<T> dA = psub(P2<T>::mk(wN[0], wN[1]), P2<T>::mk(wS[0], wS[1]));
   const P2<T> dB = psub(P2<T>::mk(wN[2], wN[3]), P2<T>::mk(wS[2], wS[3]));
   const P2<T> dC = psub(P2<T>::mk(wN[4], wN[5]), P2<T>::mk(wS[4], wS[5]));
@@ -605,8 +657,9 @@ __device__ __forceinline__ void stencil_core4(const RunK<T>& K, const MonT<T>& m
     const P2<T> Wv = P2<T>::mk(wC[2 * pp], wC[2 * pp + 1]);
     const P2<T> Nn = P2<T>::mk(wN[2 * pp + 1], wN[2 * pp + 2]);
     const P2<T> Ss = P2<T>::mk(wS[2 * pp + 1], wS[2 * pp + 2]);
-    const P2<T> XI0 = P2<T>::mk(fma((T)(gi0 + 2 * pp), K.h0, K.lo0),
-                                fma((T)(gi0 + 2 * pp + 1), K.h0, K.lo0));
+    const P2<T> XI0 = TAB ? P2<T>::mk(xc.v[2 * pp], xc.v[2 * pp + 1])
+                          : P2<T>::mk(fma((T)(ct.gi0 + 2 * pp), K.h0, K.lo0),
+                                      fma((T)(ct.gi0 + 2 * pp + 1), K.h0, K.lo0));
     X0[pp] = pfma(psub(E, Wv), K.I2H0, XI0);
     X1[pp] = pfma(psub(Nn, Ss), K.I2H1, P2<T>::s(xi1));
     const P2<T> hxx = pfma(pfma(C, K.M2, padd(E, Wv)), K.IH20, K.ONE);
@@ -644,41 +697,36 @@ __device__ __forceinline__ void stencil_core4(const RunK<T>& K, const MonT<T>& m
   // every value below stays finite there, their G - c enters the finiteness
   // sum as -c_lag, their theta weight is 0 (they are never owned), and
   // +-big offsets keep them out of the extrema.
-  const P2<T> ROWU = P2<T>::s(rowdir ? T(0) : T(1));
   const P2<T> WYO = P2<T>::s(wyo);
+  Vec4<T> kc;
+  if (TAB) kc.lds(ct.k);
   P2<T> GMX[2], GMN[2], DMN[2], GCs[2], Ms[2];
 #pragma unroll
   for (int pp = 0; pp < 2; ++pp) {
-    const P2<T> m = pmul(P2<T>::mk(uc.v[2 * pp], uc.v[2 * pp + 1]), ROWU);
+    const P2<T> uc2 = P2<T>::mk(uc.v[2 * pp], uc.v[2 * pp + 1]);
+    const P2<T> m = rowdir ? P2<T>::s(T(0)) : uc2;
     const P2<T> rd = pmul(R[pp], DD[pp]);
     const P2<T> rD = P2<T>::mk(m.x() != T(0) ? rd.x() : T(1), m.y() != T(0) ? rd.y() : T(1));
-    P2<T> GC;
-    if (K.logrhs) {
-      GC = P2<T>::mk(Fm<T>::ln(rD.x()), Fm<T>::ln(rD.y()));
-      GC = padd(GC, K.NCL);
-    } else {
-      GC = P2<T>::mk(Fm<T>::pw(K.scale_root * rD.x(), K.inv_dim) - T(1) - K.c_lag,
-                     Fm<T>::pw(K.scale_root * rD.y(), K.inv_dim) - T(1) - K.c_lag);
-    }
+    const P2<T> GC = rhs_pair<T>(K, rD);
     const P2<T> vn = pfma(GC, K.DT2, P2<T>::mk(wC[2 * pp + 1], wC[2 * pp + 2]));
     o.v[2 * pp] = vn.x();
     o.v[2 * pp + 1] = vn.y();
     A.gs2 = padd(A.gs2, GC);
     A.th2 = pfma(pmul(P2<T>::mk(wc.v[2 * pp], wc.v[2 * pp + 1]), WYO), rD, A.th2);
-    const P2<T> kmx = pfma(m, K.BIG, K.NBIG);  // 0 or -big
-    const P2<T> kmn = pfma(m, K.NBIG, K.BIG);  // 0 or +big
-    GMX[pp] = pfma(GC, m, kmx);
-    GMN[pp] = pfma(GC, m, kmn);
+    const P2<T> kmn = TAB ? P2<T>::mk(kc.v[2 * pp], kc.v[2 * pp + 1])
+                          : pfma(m, K.NBIG, K.BIG);  // 0 or +big
+    GMX[pp] = pmul(rD, m);                     // rho det or 0
+    GMN[pp] = pfma(rD, m, kmn);                // rho det or +big
     DMN[pp] = pfma(DD[pp], m, kmn);
     GCs[pp] = GC;
     Ms[pp] = m;
   }
-  A.gcmax = max3(max3(A.gcmax, GMX[0].x(), GMX[0].y()), GMX[1].x(), GMX[1].y());
-  A.gcmin = min3(min3(A.gcmin, GMN[0].x(), GMN[0].y()), GMN[1].x(), GMN[1].y());
+  A.rmax = max3(max3(A.rmax, GMX[0].x(), GMX[0].y()), GMX[1].x(), GMX[1].y());
+  A.rmin = min3(min3(A.rmin, GMN[0].x(), GMN[0].y()), GMN[1].x(), GMN[1].y());
   A.dmin = min3(min3(A.dmin, DMN[0].x(), DMN[0].y()), DMN[1].x(), DMN[1].y());
   if (K.want_l2) {
     Vec4<T> lc;
-    lc.lds(lcp);
+    lc.lds(ct.l);
 #pragma unroll
     for (int pp = 0; pp < 2; ++pp) {
       const P2<T> w = pmul(pmul(P2<T>::mk(lc.v[2 * pp], lc.v[2 * pp + 1]), P2<T>::s(wly)), Ms[pp]);
@@ -723,7 +771,7 @@ __device__ __forceinline__ void issue_hdr(const LaunchArgs& a, BandHdr<T>& H, co
 // column c sits at c + 4 (halo columns at 3 and cols + 4), rows are `SWp`
 // (a multiple of 4) wide.
 template <typename T, int NT, int SMAX>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band2d(LaunchArgs a) {
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2d(LaunchArgs a) {
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int NW = NT / 32;
   __shared__ __align__(16) T sv[SMAX];
@@ -772,7 +820,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
     T* dst = (T*)H.sd.v[H.ps.parity ^ 1];
     const int rpr = (cols + 3) >> 2;  // runs per row
     const int nruns = rows * rpr;
-    const float inv_rpr = 1.0f / (float)rpr;
+    const float inv_rpr = __fdividef(1.0f, (float)rpr);
     // transmission nodes: local index equal to one of these (-1 = none)
     const int dlx = (faces & 1) ? -1 : 0, dhx = (faces & 2) ? -1 : n0 - 1;
     const int dly = (faces & 4) ? -1 : 0, dhy = (faces & 8) ? -1 : n1 - 1;
@@ -806,7 +854,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
       const int SWp = ((cols + 3) & ~3) + 8;
       const int SH = rows + 2;
       const int cpr = SWp / VW;  // 16-byte chunks per shared row
-      const float inv_cpr = 1.0f / (float)cpr;
+      const float inv_cpr = __fdividef(1.0f, (float)cpr);
       const bool plx = faces & 1, phx = faces & 2, ply = faces & 4, phy = faces & 8;
       // (a) 16-byte asynchronous copies of the band rows (global columns
       //     i0-4 .. i0+SWp-5; chunks outside the pitched row are skipped)
@@ -821,21 +869,27 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
       cp_async_commit();
       // Per-column tables of the band (after the staged rows in shared
       // memory): theta weight of owned columns (0 elsewhere), 1 for updated
-      // columns (inside the band, not a transmission column), and the local
-      // trapezoid weight for the L2 increment.
+      // columns (inside the band, not a transmission column), the local
+      // trapezoid weight for the L2 increment, xi_x, and +big at columns
+      // that are not updated (0 elsewhere).
       const int cr = (cols + 3) & ~3;
       {
-      const T h0 = H.ph.h[0], hw0 = H.ph.hw[0];
+      const T h0 = H.ph.h[0], hw0 = H.ph.hw[0], lo0 = H.ph.lo[0];
       const int N0 = H.ph.N[0], clo0 = H.sd.clo[0], chi0 = H.sd.chi[0];
       T* const wcol = sv + SH * SWp;
       T* const ucol = wcol + cr;
       T* const lcol = ucol + cr;
+      T* const xcol = lcol + cr;
+      T* const kcol = xcol + cr;
       for (int c = tid; c < cr; c += NT) {
         const int i = i0 + c, gi = g00 + i;
         const bool valid = c < cols;
+        const bool upd = valid && i != dlx && i != dhx;
         wcol[c] = (valid && i >= clo0 && i <= chi0) ? ((gi == 0 || gi == N0 - 1) ? hw0 : h0) : T(0);
-        ucol[c] = (valid && i != dlx && i != dhx) ? T(1) : T(0);
+        ucol[c] = upd ? T(1) : T(0);
         lcol[c] = (i == 0 || i == n0 - 1) ? hw0 : h0;
+        xcol[c] = fma((T)gi, h0, lo0);
+        kcol[c] = upd ? T(0) : big_val<T>();
       }
       }
       // Transmission nodes of the band (Eq. transmission_condition3): whole
@@ -899,29 +953,27 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
           if (right) sv[r * SWp + cols + 4] = hr[q];
         }
       }
-      if (corr != T(0)) {
-        const int cl = (dlx == 0 && i0 == 0) ? 4 : -1;
-        const int ch = (dhx >= 0 && right) ? cols + 3 : -1;
-        if (cl >= 0 || ch >= 0) {
+      const int fl = H.w.flags;
+      if (corr != T(0) && fl != 0) {
+        const int r0 = (fl & 1) ? 0 : -1, r1 = (fl & 2) ? 1 : -1;
+        const int r2 = (fl & 4) ? SH - 2 : -1, r3 = (fl & 8) ? SH - 1 : -1;
+        if (fl & 48) {
+          const int cl = (fl & 16) ? 4 : -1, ch = (fl & 32) ? cols + 3 : -1;
           for (int r = tid; r < SH; r += NT) {
-            const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
-            if (jj != dly && jj != dhy) {
+            if (r != r0 && r != r1 && r != r2 && r != r3) {
               if (cl >= 0) sv[r * SWp + cl] += corr;
               if (ch >= 0) sv[r * SWp + ch] += corr;
             }
           }
         }
-        const int cand[4] = {0, 1, SH - 2, SH - 1};
+        if (fl & 15) {
+          const int rr[4] = {r0, r1, r2, r3};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int r = cand[q];
-          bool dup = r < 0 || r >= SH;
-          for (int p2 = 0; p2 < q; ++p2) dup = dup || (cand[p2] == r);
-          if (dup) continue;
-          const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
-          if (jj == dly || jj == dhy)
+          for (int q = 0; q < 4; ++q) {
+            if (rr[q] < 0) continue;
             for (int c = tid; c < SWp; c += NT)
-              if (!(left && c == 3) && !(right && c == cols + 4)) sv[r * SWp + c] += corr;
+              if (!(left && c == 3) && !(right && c == cols + 4)) sv[rr[q] * SWp + c] += corr;
+          }
         }
       }
       if (H.ph.alternating) {
@@ -929,7 +981,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
         stage_alternating<T, NT>(a, H, sv, SWp, SH, 1, i0, j0, 0, cols);
       }
       __syncthreads();  // S2: band staged
-      const T c_lag = (T)H.ps.c_lag;
       const T h0 = H.ph.h[0], h1 = H.ph.h[1];
       const T hw0 = H.ph.hw[0], hw1 = H.ph.hw[1];
       const int N0 = H.ph.N[0], N1 = H.ph.N[1];
@@ -938,21 +989,28 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
       const T* const wcol = sv + SH * SWp;
       const T* const ucol = wcol + cr;
       const T* const lcol = ucol + cr;
+      const T* const xcol = lcol + cr;
+      const T* const kcol = xcol + cr;
 
       // partial sums: theta, sum of (G - c) over updated nodes (a non-finite
       // value anywhere makes it non-finite), extrema of G - c, min det
       const RunK<T> K = make_runk<T>(H.ph, H.ps, phase);
       RunAcc<T> A = RunAcc<T>::zero();
-      for (int q = tid; q < nruns; q += NT) {
-        const int r = qdiv(q, rpr, inv_rpr), c0 = (q - r * rpr) * 4;
+      // transmission rows (only a band's first or last row can be one) are
+      // written by the transmission pass and skipped here
+      const int rlo = (j0 == dly) ? 1 : 0;
+      const int rhi = (j0 + rows - 1 == dhy) ? rows - 1 : rows;
+      const int nrun_u = rhi > rlo ? (rhi - rlo) * rpr : 0;
+      for (int q = tid; q < nrun_u; q += NT) {
+        const int rq = qdiv(q, rpr, inv_rpr), r = rlo + rq, c0 = (q - rq * rpr) * 4;
         const int j = j0 + r, gj = g01 + j;
-        const bool rowdir = (j == dly || j == dhy);
         const T wyo = (j >= clo1 && j <= chi1) ? ((gj == 0 || gj == N1 - 1) ? hw1 : h1) : T(0);
         const T wly = (j == 0 || j == n1 - 1) ? hw1 : h1;
         Vec4<T> o;
-        stencil_run4<T>(K, H.ph.mon, sv + (r + 1) * SWp + c0 + 4, SWp, wcol + c0, ucol + c0,
-                        lcol + c0, rowdir, wyo, wly, fma((T)gj, K.h1, K.lo1), g00 + i0 + c0, o, A);
-        if (run && !rowdir) {
+        const ColTab<T> ct{wcol + c0, ucol + c0, lcol + c0, xcol + c0, kcol + c0, 0};
+        stencil_run4<T, true>(K, H.ph.mon, sv + (r + 1) * SWp + c0 + 4, SWp, ct, false, wyo,
+                              wly, fma((T)gj, K.h1, K.lo1), o, A);
+        if (run) {
           T* const q = dst + j * pitch + i0 + c0;
           if ((i0 + c0 <= dlx) || (i0 + c0 + 3 >= dhx && dhx >= 0)) {
             // a run holding a transmission column: updated nodes only
@@ -966,22 +1024,19 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_band
           }
         }
       }
-      const P2<T> th2 = A.th2, gs2 = A.gs2;
-      const T gcmax = A.gcmax, gcmin = A.gcmin;
-      acc.dmin = A.dmin;
+      A.fold(K, acc);
       l2a = A.l2a;
       l2b = A.l2b;
       ws = A.ws;
-      th = th2.x() + th2.y();
-      if (gcmax > -big_val<T>()) acc.gmax = gcmax + c_lag;
-      if (gcmin < big_val<T>()) acc.gmin = gcmin + c_lag;
-      if (!isfinite(gs2.x() + gs2.y())) acc.nf += 1;
+      th = A.th2.x() + A.th2.y();
     }
     // tile record and arrival
     th = warp_sum(th);
-    l2a = warp_sum(l2a);
-    l2b = warp_sum(l2b);
-    ws = warp_sum(ws);
+    if (H.ph.stop_norm == PMA_STOP_L2_INCREMENT) {
+      l2a = warp_sum(l2a);
+      l2b = warp_sum(l2b);
+      ws = warp_sum(ws);
+    }
     const T gmax = warp_max(acc.gmax), gmin = warp_min(acc.gmin), dmin = warp_min(acc.dmin);
     const int nf = warp_isum(acc.nf);
     if (lane == 0) {
@@ -1286,7 +1341,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_res2
 
   const int rpr = cr >> 2;
   const int nruns = n1 * rpr;
-  const float inv_rpr = 1.0f / (float)rpr;
+  const float inv_rpr = __fdividef(1.0f, (float)rpr);
   bool computed = false;
   int dpar = -1;  // buffer whose transmission values carry the last correction
   for (int it = 0;; ++it) {
@@ -1336,8 +1391,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_res2
         const T wyo = (j >= clo1 && j <= chi1) ? ((gj == 0 || gj == N1 - 1) ? hw1 : h1) : T(0);
         const T wly = (j == 0 || j == n1 - 1) ? hw1 : h1;
         Vec4<T> o;
-        stencil_run4<T>(K, ph.mon, cur + (r + 1) * SWp + c0 + 4, SWp, wcol + c0, ucol + c0,
-                        lcol + c0, rowdir, wyo, wly, fma((T)gj, K.h1, K.lo1), g00 + c0, o, A);
+        const ColTab<T> ct{wcol + c0, ucol + c0, lcol + c0, nullptr, nullptr, g00 + c0};
+        stencil_run4<T, false>(K, ph.mon, cur + (r + 1) * SWp + c0 + 4, SWp, ct, rowdir, wyo,
+                               wly, fma((T)gj, K.h1, K.lo1), o, A);
         if (run && !rowdir) {
           T* const d = nxt + (r + 1) * SWp + c0 + 4;
           const int jm = (ply && j == 1) ? -1 : ((phy && j == n1 - 2) ? n1 : -2);
@@ -1363,10 +1419,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_res2
         }
       }
       T th = A.th2.x() + A.th2.y();
-      Acc<T> acc{-big_val<T>(), big_val<T>(), A.dmin, 0};
-      if (A.gcmax > -big_val<T>()) acc.gmax = A.gcmax + K.c_lag;
-      if (A.gcmin < big_val<T>()) acc.gmin = A.gcmin + K.c_lag;
-      if (!isfinite(A.gs2.x() + A.gs2.y())) acc.nf += 1;
+      Acc<T> acc{-big_val<T>(), big_val<T>(), big_val<T>(), 0};
+      A.fold(K, acc);
       tile_reduce<T, NT>(th, A.l2a, A.l2b, A.ws, acc, &rec[it & 1], me.sub, red_t, red_f, red_i);
       if (tid == 0) act[it & 1] = 1;
     } else {
@@ -1467,7 +1521,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
     const int cr = (cols + 3) & ~3;
     const int rpr = cr >> 2;
     const int nruns = rows * rpr;
-    const float inv_rpr = 1.0f / (float)rpr;
+    const float inv_rpr = __fdividef(1.0f, (float)rpr);
     const int dlx = (faces & 1) ? -1 : 0, dhx = (faces & 2) ? -1 : n0 - 1;
     const int dly = (faces & 4) ? -1 : 0, dhy = (faces & 8) ? -1 : n1 - 1;
     const int dlz = (faces & 16) ? -1 : 0, dhz = (faces & 32) ? -1 : n2 - 1;
@@ -1502,7 +1556,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
       const int SWp = cr + 8, SHY = rows + 2, SHZ = depth + 2;
       const int PS = SHY * SWp;
       const int cpr = SWp / VW;
-      const float inv_cpr = 1.0f / (float)cpr;
+      const float inv_cpr = __fdividef(1.0f, (float)cpr);
       const int nrow = SHZ * SHY;
       const float inv_shy = 1.0f / (float)SHY;
       const bool plx = faces & 1, phx = faces & 2, ply = faces & 4, phy = faces & 8;
@@ -1872,15 +1926,19 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
 }
 
 // ---------------------------------------------------------------- dispatch
-// Compiled shapes.  2D: (threads, band nodes FP32, band nodes FP64); the
-// staged band plus halo is at most 3x the band nodes.  3D: (TX, TY, TZ).
-#define PMA_T2D(X) X(128, 2048, 1024) X(96, 1536, 768) X(128, 2560, 1280) X(128, 1024, 512)
+// Compiled shapes.  2D: (threads, band nodes FP32, band nodes FP64, shared
+// elements per band node x 10): the staged band plus halo and the column
+// tables fit in nodes x factor / 10 elements (bands get fewer rows, or
+// narrower strips, where the halo would not fit).
+#define PMA_T2D(X) X(128, 3072, 1536, 16) X(128, 2048, 1024, 30) X(128, 4096, 2048, 14) \
+                   X(128, 5120, 2560, 14)
+#define PMA_SMAX(n, f) (((n) * (f) / 10) & ~3)
 // 3D: (threads, nodes per plane box, planes FP32, planes FP64, dynamic
 // shared memory in KiB for the staged box and the column tables).
 #define PMA_T3D(X) X(128, 512, 8, 4, 64) X(128, 512, 16, 8, 96) X(256, 1024, 8, 4, 96)
 
-static const int k_t2d[][3] = {
-#define E(a, b, c) {a, b, c},
+static const int k_t2d[][4] = {
+#define E(a, b, c, f) {a, b, c, f},
     PMA_T2D(E)
 #undef E
 };
@@ -1896,10 +1954,10 @@ Tile2D tile2d_shape(int id, bool fp64) {
   Tile2D t;
   t.threads = k_t2d[id][0];
   t.nodes = fp64 ? k_t2d[id][2] : k_t2d[id][1];
-  t.smax = 3 * t.nodes;
-  // a one-row band plus halo and the three column tables must fit:
-  // 3 * (cols + 8) + 3 * cols <= smax, cols % 4 == 0
-  const int cmax = ((t.smax - 24) / 6) & ~3;
+  t.smax = PMA_SMAX(t.nodes, k_t2d[id][3]);
+  // a one-row band plus halo and the five column tables must fit:
+  // 3 * (cols + 8) + 5 * cols <= smax, cols % 4 == 0
+  const int cmax = ((t.smax - 24) / 8) & ~3;
   t.cols = cmax < 1024 ? cmax : 1024;
   return t;
 }
@@ -1920,13 +1978,13 @@ static const void* sweep_fn(int dim, int id, int* nthreads, int* dyn) {
   int k = 0;
   *dyn = 0;
   if (dim == 2) {
-#define E(a, b, c)                                                         \
+#define E(a, b, c, f)                                                      \
   if (k++ == id) {                                                         \
     *nthreads = (a);                                                       \
     if constexpr (sizeof(T) == 8)                                          \
-      return (const void*)k_band2d<T, a, 3 * (c)>;                         \
+      return (const void*)k_band2d<T, a, PMA_SMAX(c, f)>;                  \
     else                                                                   \
-      return (const void*)k_band2d<T, a, 3 * (b)>;                         \
+      return (const void*)k_band2d<T, a, PMA_SMAX(b, f)>;                  \
   }
     PMA_T2D(E)
 #undef E
