@@ -291,6 +291,8 @@ struct pma_ctx {
 
   // tables
   SubDesc* d_subs = nullptr;
+  NbEnt* d_nb = nullptr;
+  size_t nb_cap = 0;
   size_t subs_cap = 0;
   WorkItem* d_work[NUM_CLS] = {};
   Partial* d_part[NUM_CLS] = {};
@@ -304,6 +306,7 @@ struct pma_ctx {
   int grid[NUM_CLS] = {};
   int tile_id[NUM_CLS] = {};
   std::vector<SubDesc> h_subs;
+  std::vector<NbEnt> h_nb;
   std::vector<WorkItem> h_work[NUM_CLS];
   bool dirty = true;
   long long dead_tiles = 0, live_tiles = 0;
@@ -591,10 +594,39 @@ void push_items(const HostSub& hs, int dim, bool fp64, int tile_id, int sidx, in
   }
 }
 
+// Neighbour entries of the subdomains subs[0..n) of one problem (blocks in
+// raster order over parts), appended to `out` (see NbEnt).
+void fill_nb(const SubDesc* subs, int n, const int parts[3], int esize, std::vector<NbEnt>& out) {
+  for (int s = 0; s < n; ++s) {
+    const SubDesc& me = subs[s];
+    for (int q = 0; q < kNbPerSub; ++q) {
+      const int d[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+      int k[3];
+      bool ok = true;
+      for (int a = 0; a < 3; ++a) {
+        k[a] = me.k[a] + d[a];
+        ok = ok && k[a] >= 0 && k[a] < parts[a];
+      }
+      NbEnt e{};
+      if (ok) {
+        const SubDesc& o = subs[(k[2] * parts[1] + k[1]) * parts[0] + k[0]];
+        const long long pitch = o.pitch, plane = (long long)o.pitch * o.n[1];
+        const long long c0 = (me.g0[0] - o.g0[0]) + pitch * (me.g0[1] - o.g0[1]) +
+                             plane * (me.g0[2] - o.g0[2]);
+        for (int p = 0; p < 2; ++p) e.v[p] = (const char*)o.v[p] + c0 * esize;
+        e.pitch = (int)pitch;
+        e.plane = (int)plane;
+      }
+      out.push_back(e);
+    }
+  }
+}
+
 // Rebuild subdomain table, work lists and problem descriptors for the
 // current active + finished requests.  Only active requests get tiles.
 pma_status rebuild(pma_ctx* c) {
   c->h_subs.clear();
+  c->h_nb.clear();
   for (int k = 0; k < NUM_CLS; ++k) {
     c->h_work[k].clear();
     c->h_fin[k].clear();
@@ -635,6 +667,7 @@ pma_status rebuild(pma_ctx* c) {
       c->h_subs.push_back(sd);
     }
     pd.tile_end = (int)wl.size();
+    fill_nb(c->h_subs.data() + pd.sub_base, (int)r.subs.size(), pd.parts, r.esize, c->h_nb);
     if (live) {
       c->live_tiles += pd.tile_end - pd.tile_begin;
       c->h_fin[r.cls].push_back(r.slot);
@@ -644,9 +677,13 @@ pma_status rebuild(pma_ctx* c) {
   }
   pma_status st;
   if ((st = ensure_buf(&c->d_subs, &c->subs_cap, c->h_subs.size() + 1)) != PMA_OK) return st;
-  if (!c->h_subs.empty())
+  if ((st = ensure_buf(&c->d_nb, &c->nb_cap, c->h_nb.size() + 1)) != PMA_OK) return st;
+  if (!c->h_subs.empty()) {
     PMA_CK(cudaMemcpyAsync(c->d_subs, c->h_subs.data(), sizeof(SubDesc) * c->h_subs.size(),
                            cudaMemcpyHostToDevice, c->stream));
+    PMA_CK(cudaMemcpyAsync(c->d_nb, c->h_nb.data(), sizeof(NbEnt) * c->h_nb.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+  }
   for (int k = 0; k < NUM_CLS; ++k) {
     const size_t cap = c->work_cap[k];
     if ((st = ensure_buf(&c->d_work[k], &c->work_cap[k], c->h_work[k].size() + 1)) != PMA_OK)
@@ -676,7 +713,7 @@ pma_status rebuild(pma_ctx* c) {
                          cudaMemcpyHostToDevice, c->stream));
   PMA_CK(cudaMemcpyAsync(c->d_hotd, c->h_hotd.data(), sizeof(ProbHot<double>) * c->slot_cap,
                          cudaMemcpyHostToDevice, c->stream));
-  c->stats.h2d_bytes += (double)(sizeof(SubDesc) * c->h_subs.size() +
+  c->stats.h2d_bytes += (double)(sizeof(SubDesc) * c->h_subs.size() + sizeof(NbEnt) * c->h_nb.size() +
                                  (sizeof(ProbDesc) + sizeof(ProbHot<float>) +
                                   sizeof(ProbHot<double>)) * c->slot_cap);
   for (int k = 0; k < NUM_CLS; ++k) c->stats.h2d_bytes += (double)sizeof(WorkItem) * c->nwork[k];
@@ -825,6 +862,7 @@ LaunchArgs args_for(pma_ctx* c, int k, int t0, int n) {
   a.t0 = t0;
   a.nwork = n;
   a.subs = c->d_subs;
+  a.nb = c->d_nb;
   a.probs = c->d_probs;
   a.st = c->d_state;
   a.part = c->d_part[k];
@@ -1222,6 +1260,7 @@ pma_status pma_destroy(pma_ctx* c) {
   cudaFree(c->d_hotd);
   cudaFreeHost(c->h_state);
   cudaFree(c->d_subs);
+  cudaFree(c->d_nb);
   for (int k = 0; k < NUM_CLS; ++k) {
     cudaFree(c->d_work[k]);
     cudaFree(c->d_part[k]);
@@ -1757,6 +1796,7 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   // scratch layout; everything must fit the fixed array
   Carve cv;
   const size_t o_subs = cv.take(sizeof(SubDesc) * subs.size());
+  const size_t o_nb = cv.take(sizeof(NbEnt) * kNbPerSub * subs.size());
   const size_t o_work = cv.take(sizeof(WorkItem) * work.size());
   const size_t o_part = cv.take(sizeof(Partial) * work.size());
   const size_t o_prob = cv.take(sizeof(ProbDesc));
@@ -1782,6 +1822,8 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   }
   ProbDesc pd;
   fill_probdesc(r, pd);
+  std::vector<NbEnt> nb;
+  fill_nb(subs.data(), (int)subs.size(), pd.parts, r.esize, nb);
   pd.sub_base = 0;
   pd.tile_begin = 0;
   pd.tile_end = (int)work.size();
@@ -1798,6 +1840,8 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   // upload (clears the counters and the problem scalars of any earlier call)
   PMA_CK(cudaMemcpyAsync(B + o_subs, subs.data(), sizeof(SubDesc) * subs.size(),
                          cudaMemcpyHostToDevice, s));
+  PMA_CK(cudaMemcpyAsync(B + o_nb, nb.data(), sizeof(NbEnt) * nb.size(), cudaMemcpyHostToDevice,
+                         s));
   PMA_CK(cudaMemcpyAsync(B + o_work, work.data(), sizeof(WorkItem) * work.size(),
                          cudaMemcpyHostToDevice, s));
   PMA_CK(cudaMemcpyAsync(B + o_prob, &pd, sizeof(pd), cudaMemcpyHostToDevice, s));
@@ -1821,6 +1865,7 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   la.t0 = 0;
   la.nwork = (int)work.size();
   la.subs = (const SubDesc*)(B + o_subs);
+  la.nb = (const NbEnt*)(B + o_nb);
   la.probs = (const ProbDesc*)(B + o_prob);
   la.st = (ProbState*)(B + o_st);
   la.part = (Partial*)(B + o_part);

@@ -212,6 +212,19 @@ cudaError_t launch_res2d(bool fp64, int id, const ResArgs& a, int nclusters, int
                          int smem_bytes, cudaStream_t s);
 
 // Kernel launch entry points (pma_kernels.cu).
+// Owners of transmission nodes: for every subdomain, kNbPerSub entries, one
+// per block offset (dx, dy, dz) in {-1, 0, 1}^3 (entry 13 + dx + 3 dy + 9 dz):
+// the neighbouring block's two state buffers, shifted so that the owner's
+// value at local node (i, j, l) of THIS subdomain is element
+// i + pitch j + plane l of v[parity]; null where there is no such block.
+struct alignas(16) NbEnt {
+  const void* v[2];
+  int pitch, plane;
+  long long pad;
+};
+constexpr int kNbPerSub = 27;
+static_assert(sizeof(NbEnt) == 32, "neighbour entry is 32 bytes");
+
 struct LaunchArgs {
   const ProbHot<float>* hotf;
   const ProbHot<double>* hotd;
@@ -219,6 +232,7 @@ struct LaunchArgs {
   int t0;                // first work item of this launch
   int nwork;             // work items of this launch
   const SubDesc* subs;
+  const NbEnt* nb;       // kNbPerSub entries per subdomain
   const ProbDesc* probs;
   ProbState* st;
   Partial* part;

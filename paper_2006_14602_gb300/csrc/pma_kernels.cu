@@ -324,22 +324,20 @@ cudaError_t launch_finish(const int* list, int n, const SubDesc* subs, const Pro
 }
 
 // ---------------------------------------------------------------- helpers
-// Owner's value at a global node (parallel transmission: previous step).
-// A node outside this subdomain's core along an axis belongs to the
+// Owner's value at local node (i, j, l) of the item's subdomain (parallel
+// transmission: previous step), through the subdomain's neighbour table.  A
+// node outside this subdomain's core along an axis belongs to the
 // neighbouring block on that side (cores hold >= ceil(o/2)+1 nodes).
 template <typename T>
 __device__ __forceinline__ T gather_owner(const LaunchArgs& a, const SmemHdr<T>& S, int i, int j,
                                           int l) {
-  const int kx = S.sd.k[0] + (i < S.sd.clo[0] ? -1 : (i > S.sd.chi[0] ? 1 : 0));
-  const int ky = S.sd.k[1] + (j < S.sd.clo[1] ? -1 : (j > S.sd.chi[1] ? 1 : 0));
-  const int kz = S.sd.k[2] + (l < S.sd.clo[2] ? -1 : (l > S.sd.chi[2] ? 1 : 0));
-  const SubDesc* od = a.subs + S.ph.sub_base + (kz * S.ph.parts[1] + ky) * S.ph.parts[0] + kx;
-  const int ox = S.sd.g0[0] + i - __ldg(&od->g0[0]);
-  const int oy = S.sd.g0[1] + j - __ldg(&od->g0[1]);
-  const int oz = S.sd.g0[2] + l - __ldg(&od->g0[2]);
-  const long long pitch = __ldg(&od->pitch), on1 = __ldg(&od->n[1]);
-  const T* ov = (const T*)od->v[S.ps.parity];
-  return __ldcg(ov + ox + pitch * (oy + on1 * oz));
+  const int qx = i < S.sd.clo[0] ? 0 : (i > S.sd.chi[0] ? 2 : 1);
+  const int qy = j < S.sd.clo[1] ? 0 : (j > S.sd.chi[1] ? 2 : 1);
+  const int qz = l < S.sd.clo[2] ? 0 : (l > S.sd.chi[2] ? 2 : 1);
+  const NbEnt* e = a.nb + S.w.sub * kNbPerSub + qx + 3 * qy + 9 * qz;
+  const T* ov = (const T*)__ldg((const unsigned long long*)&e->v[S.ps.parity]);
+  const int2 pp = __ldg((const int2*)&e->pitch);
+  return __ldcg(ov + i + (long long)pp.x * j + (long long)pp.y * l);
 }
 
 // Alternating transmission (Algorithm 1): a transmission node whose owner
