@@ -579,7 +579,7 @@ void push_items(const HostSub& hs, int dim, bool fp64, int tile_id, int sidx, in
       const int cr = (cols + 3) & ~3;
       const int swp = cr + 8;
       int rows = std::max(1, std::min(hs.n[1], t3.xy / cr));
-      while (rows > 1 && ((rows + 2) * swp * (t3.tz + 2) + 3 * cr > t3.smax ||
+      while (rows > 1 && ((rows + 2) * swp * (t3.tz + 2) + 5 * cr > t3.smax ||
                           (rows + 2) * (t3.tz + 2) > 8 * t3.threads))
         --rows;
       for (int y = 0; y < hs.n[1]; y += rows) {

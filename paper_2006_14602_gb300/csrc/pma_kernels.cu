@@ -1466,8 +1466,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_res2
 // on the box perimeter).  Each thread takes runs of 4 consecutive x-nodes of
 // one row and marches them through the planes; per plane it reads the 46
 // values of the 19-point stencils of its 4 nodes with aligned vector loads.
-template <typename T, int NT, int TZ>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3d(LaunchArgs a) {
+template <typename T, int NT, int TZ, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int NW = NT / 32;
   constexpr int HMAX = 8;  // halo rows per thread (host: (rows+2)(TZ+2) <= 8 NT)
@@ -1667,8 +1667,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
         __syncthreads();
         stage_alternating<T, NT>(a, H, sv, SWp, SHY, SHZ, i0, j0, k0, cols);
       }
-      const T c_lag = (T)H.ps.c_lag, dt = H.ph.dt;
-      const T scale_root = (T)(H.ph.vol / (T)H.ps.theta_prev);
       const T lo0 = H.ph.lo[0], lo1 = H.ph.lo[1], lo2 = H.ph.lo[2];
       const T h0 = H.ph.h[0], h1 = H.ph.h[1], h2 = H.ph.h[2];
       const T hw0 = H.ph.hw[0], hw1 = H.ph.hw[1], hw2 = H.ph.hw[2];
@@ -1677,28 +1675,30 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
       const int clo2 = H.sd.clo[2], chi2 = H.sd.chi[2];
       const bool want_l2 = H.ph.stop_norm == PMA_STOP_L2_INCREMENT;
       const bool run = phase == PH_RUN;
-      const bool logrhs = H.ph.rhs == PMA_RHS_LOG || !run;
-      const T inv_dim = T(1) / (T)H.ph.dim;
-      const int nterms = H.ph.mon.nterms;
-      bool fast = (H.ph.mon.kind == PMA_MON_SUM);
-      for (int q = 0; q < kMaxTerms; ++q)
-        if (q < nterms && H.ph.mon.t[q].type != PMA_TERM_BUMP && H.ph.mon.t[q].type != PMA_TERM_RING)
-          fast = false;
-      // column tables after the staged planes
+      const RunK<T> K = make_runk<T>(H.ph, H.ps, phase);
+      const int nterms = K.nterms;
+      const bool fast = K.fast;
+      // column tables after the staged planes: theta weight of owned
+      // columns (0 elsewhere), 1 at updated columns (else 0), the local
+      // trapezoid weight, xi_x, and +big at columns that are not updated
       T* wcol = sv + SHZ * PS;
       T* ucol = wcol + cr;
       T* lcol = ucol + cr;
+      T* xcol = lcol + cr;
+      T* kcol = xcol + cr;
       for (int c = tid; c < cr; c += NT) {
         const int i = i0 + c, gi = g00 + i;
         const bool valid = c < cols;
+        const bool upd = valid && i != dlx && i != dhx;
         wcol[c] = (valid && i >= clo0 && i <= chi0) ? ((gi == 0 || gi == N0 - 1) ? hw0 : h0) : T(0);
-        ucol[c] = (valid && i != dlx && i != dhx) ? T(1) : T(0);
+        ucol[c] = upd ? T(1) : T(0);
         lcol[c] = (i == 0 || i == n0 - 1) ? hw0 : h0;
+        xcol[c] = fma((T)gi, h0, lo0);
+        kcol[c] = upd ? T(0) : big_val<T>();
       }
       __syncthreads();  // box staged
-      P2<T> th2 = P2<T>::s(T(0)), gs2 = P2<T>::s(T(0));
-      T gcmax = -big_val<T>(), gcmin = big_val<T>();
-      const P2<T> NCL = P2<T>::s(-c_lag), DT2 = P2<T>::s(dt);
+      RunAcc<T> A = RunAcc<T>::zero();
+      const P2<T> DT2 = K.DT2;
       const P2<T> M2 = P2<T>::s(T(-2)), ONE = P2<T>::s(T(1));
       const P2<T> I2H0 = P2<T>::s(H.ph.inv2h[0]), I2H1 = P2<T>::s(H.ph.inv2h[1]);
       const P2<T> I2H2 = P2<T>::s(H.ph.inv2h[2]);
@@ -1706,22 +1706,24 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
       const P2<T> IH22 = P2<T>::s(H.ph.invh2[2]);
       const P2<T> I4XY = P2<T>::s(H.ph.inv4hh[0]), I4XZ = P2<T>::s(H.ph.inv4hh[1]);
       const P2<T> I4YZ = P2<T>::s(H.ph.inv4hh[2]);
-      const P2<T> BIG = P2<T>::s(big_val<T>()), NBIG = P2<T>::s(-big_val<T>());
-      for (int q = tid; q < nruns; q += NT) {
-        const int r = qdiv(q, rpr, inv_rpr), c0 = (q - r * rpr) * 4;
+      // transmission rows and planes (only a box's first or last row or
+      // plane can be one) are written by the transmission pass, not here
+      const int rlo = (j0 == dly) ? 1 : 0, rhi = (j0 + rows - 1 == dhy) ? rows - 1 : rows;
+      const int llo = (k0 == dlz) ? 1 : 0, lhi = (k0 + depth - 1 == dhz) ? depth - 1 : depth;
+      const int nrun_u = rhi > rlo ? (rhi - rlo) * rpr : 0;
+      for (int q = tid; q < nrun_u; q += NT) {
+        const int rq = qdiv(q, rpr, inv_rpr), r = rlo + rq, c0 = (q - rq * rpr) * 4;
         const int j = j0 + r, gj = g01 + j;
-        Vec4<T> wc, uc;
+        Vec4<T> wc, uc, xc;
         wc.lds(wcol + c0);
         uc.lds(ucol + c0);
-        const bool rowdir = (j == dly || j == dhy);
+        xc.lds(xcol + c0);
         const T wyo = (j >= clo1 && j <= chi1) ? ((gj == 0 || gj == N1 - 1) ? hw1 : h1) : T(0);
         const T xi1 = fma((T)gj, h1, lo1);
-        const int gi0 = g00 + i0 + c0;
         P2<T> XI0[2];
 #pragma unroll
-        for (int pp = 0; pp < 2; ++pp)
-          XI0[pp] = P2<T>::mk(fma((T)(gi0 + 2 * pp), h0, lo0), fma((T)(gi0 + 2 * pp + 1), h0, lo0));
-        for (int l = 0; l < depth; ++l) {
+        for (int pp = 0; pp < 2; ++pp) XI0[pp] = P2<T>::mk(xc.v[2 * pp], xc.v[2 * pp + 1]);
+        for (int l = llo; l < lhi; ++l) {
           const int kk = k0 + l, gk = g02 + kk;
           const T* p = sv + (l + 1) * PS + (r + 1) * SWp + c0 + 4;
           // plane z: rows j-1, j, j+1, columns c0-1 .. c0+4
@@ -1748,7 +1750,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
             uS.lds(pu - SWp);
             uN.lds(pu + SWp);
           }
-          const bool plndir = (kk == dlz || kk == dhz);
           const T wzo = (kk >= clo2 && kk <= chi2) ? ((gk == 0 || gk == N2 - 1) ? hw2 : h2) : T(0);
           const T xi2 = fma((T)gk, h2, lo2);
           P2<T> X0[2], X1[2], X2[2], DD[2], R[2];
@@ -1807,39 +1808,34 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
               R[pp] = P2<T>::mk(rho_at<T>(H.ph.mon, X0[pp].x(), X1[pp].x(), X2[pp].x()),
                                 rho_at<T>(H.ph.mon, X0[pp].y(), X1[pp].y(), X2[pp].y()));
           }
-          // masks: 1 at updated nodes, 0 elsewhere; no selects per node but
-          // rho det := 1 at the others (see stencil_run4)
-          Vec4<T> o;
-          const P2<T> ROWU = P2<T>::s((rowdir || plndir) ? T(0) : T(1));
+          // masks: 1 at updated nodes, 0 elsewhere (columns only: the
+          // transmission rows and planes are skipped); rho det := 1 at the
+          // others (see stencil_core4)
+          Vec4<T> o, kc;
+          kc.lds(kcol + c0);
           const P2<T> WYZ = P2<T>::s(wyo * wzo);
           P2<T> GMX[2], GMN[2], DMN[2], GCs[2], Ms[2];
 #pragma unroll
           for (int pp = 0; pp < 2; ++pp) {
-            const P2<T> m = pmul(P2<T>::mk(uc.v[2 * pp], uc.v[2 * pp + 1]), ROWU);
+            const P2<T> m = P2<T>::mk(uc.v[2 * pp], uc.v[2 * pp + 1]);
             const P2<T> rd = pmul(R[pp], DD[pp]);
             const P2<T> rD = P2<T>::mk(m.x() != T(0) ? rd.x() : T(1), m.y() != T(0) ? rd.y() : T(1));
-            P2<T> GC;
-            if (logrhs) {
-              GC = padd(P2<T>::mk(Fm<T>::ln(rD.x()), Fm<T>::ln(rD.y())), NCL);
-            } else {
-              GC = P2<T>::mk(Fm<T>::pw(scale_root * rD.x(), inv_dim) - T(1) - c_lag,
-                             Fm<T>::pw(scale_root * rD.y(), inv_dim) - T(1) - c_lag);
-            }
+            const P2<T> GC = rhs_pair<T>(K, rD);
             const P2<T> vn = pfma(GC, DT2, P2<T>::mk(cC[2 * pp + 1], cC[2 * pp + 2]));
             o.v[2 * pp] = vn.x();
             o.v[2 * pp + 1] = vn.y();
-            gs2 = padd(gs2, GC);
-            th2 = pfma(pmul(P2<T>::mk(wc.v[2 * pp], wc.v[2 * pp + 1]), WYZ), rD, th2);
-            const P2<T> kmx = pfma(m, BIG, NBIG), kmn = pfma(m, NBIG, BIG);
-            GMX[pp] = pfma(GC, m, kmx);
-            GMN[pp] = pfma(GC, m, kmn);
+            A.gs2 = padd(A.gs2, GC);
+            A.th2 = pfma(pmul(P2<T>::mk(wc.v[2 * pp], wc.v[2 * pp + 1]), WYZ), rD, A.th2);
+            const P2<T> kmn = P2<T>::mk(kc.v[2 * pp], kc.v[2 * pp + 1]);  // 0 or +big
+            GMX[pp] = pmul(rD, m);
+            GMN[pp] = pfma(rD, m, kmn);
             DMN[pp] = pfma(DD[pp], m, kmn);
             GCs[pp] = GC;
             Ms[pp] = m;
           }
-          gcmax = max3(max3(gcmax, GMX[0].x(), GMX[0].y()), GMX[1].x(), GMX[1].y());
-          gcmin = min3(min3(gcmin, GMN[0].x(), GMN[0].y()), GMN[1].x(), GMN[1].y());
-          acc.dmin = min3(min3(acc.dmin, DMN[0].x(), DMN[0].y()), DMN[1].x(), DMN[1].y());
+          A.rmax = max3(max3(A.rmax, GMX[0].x(), GMX[0].y()), GMX[1].x(), GMX[1].y());
+          A.rmin = min3(min3(A.rmin, GMN[0].x(), GMN[0].y()), GMN[1].x(), GMN[1].y());
+          A.dmin = min3(min3(A.dmin, DMN[0].x(), DMN[0].y()), DMN[1].x(), DMN[1].y());
           if (want_l2) {
             Vec4<T> lc;
             lc.lds(lcol + c0);
@@ -1848,15 +1844,15 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
             for (int pp = 0; pp < 2; ++pp) {
               const P2<T> w = pmul(pmul(P2<T>::mk(lc.v[2 * pp], lc.v[2 * pp + 1]), P2<T>::s(wl)), Ms[pp]);
               const P2<T> d = pmul(GCs[pp], Ms[pp]);
-              l2a = fma(w.x() * d.x(), d.x(), l2a);
-              l2b = fma(w.x(), d.x(), l2b);
-              ws += w.x();
-              l2a = fma(w.y() * d.y(), d.y(), l2a);
-              l2b = fma(w.y(), d.y(), l2b);
-              ws += w.y();
+              A.l2a = fma(w.x() * d.x(), d.x(), A.l2a);
+              A.l2b = fma(w.x(), d.x(), A.l2b);
+              A.ws += w.x();
+              A.l2a = fma(w.y() * d.y(), d.y(), A.l2a);
+              A.l2b = fma(w.y(), d.y(), A.l2b);
+              A.ws += w.y();
             }
           }
-          if (run && !rowdir && !plndir) {
+          if (run) {
             T* const q = dst + kk * ppitch + j * pitch + i0 + c0;
             if ((i0 + c0 <= dlx) || (i0 + c0 + 3 >= dhx && dhx >= 0)) {
 #pragma unroll
@@ -1870,16 +1866,19 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
           }
         }
       }
-      th = th2.x() + th2.y();
-      if (gcmax > -big_val<T>()) acc.gmax = gcmax + c_lag;
-      if (gcmin < big_val<T>()) acc.gmin = gcmin + c_lag;
-      if (!isfinite(gs2.x() + gs2.y())) acc.nf += 1;
+      A.fold(K, acc);
+      l2a = A.l2a;
+      l2b = A.l2b;
+      ws = A.ws;
+      th = A.th2.x() + A.th2.y();
     }
     // tile record
     th = warp_sum(th);
-    l2a = warp_sum(l2a);
-    l2b = warp_sum(l2b);
-    ws = warp_sum(ws);
+    if (H.ph.stop_norm == PMA_STOP_L2_INCREMENT) {
+      l2a = warp_sum(l2a);
+      l2b = warp_sum(l2b);
+      ws = warp_sum(ws);
+    }
     const T gmax = warp_max(acc.gmax), gmin = warp_min(acc.gmin), dmin = warp_min(acc.dmin);
     const int nf = warp_isum(acc.nf);
     if (lane == 0) {
@@ -1932,16 +1931,17 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 384 : 256) / NT) k_band3
                    X(128, 5120, 2560, 14)
 #define PMA_SMAX(n, f) (((n) * (f) / 10) & ~3)
 // 3D: (threads, nodes per plane box, planes FP32, planes FP64, dynamic
-// shared memory in KiB for the staged box and the column tables).
-#define PMA_T3D(X) X(128, 512, 8, 4, 64) X(128, 512, 16, 8, 96) X(256, 1024, 8, 4, 96)
+// shared memory in KiB for the staged box and the column tables, FP32 CTAs
+// per SM the registers are budgeted for; FP64 budgets for 2).
+#define PMA_T3D(X) X(128, 512, 8, 4, 32, 3) X(128, 512, 8, 4, 32, 4) X(128, 512, 8, 4, 64, 3)
 
 static const int k_t2d[][4] = {
 #define E(a, b, c, f) {a, b, c, f},
     PMA_T2D(E)
 #undef E
 };
-static const int k_t3d[][5] = {
-#define E(a, b, c, d, e) {a, b, c, d, e},
+static const int k_t3d[][6] = {
+#define E(a, b, c, d, e, m) {a, b, c, d, e, m},
     PMA_T3D(E)
 #undef E
 };
@@ -1965,8 +1965,8 @@ Tile3D tile3d_shape(int id, bool fp64) {
   t.xy = k_t3d[id][1];
   t.tz = fp64 ? k_t3d[id][3] : k_t3d[id][2];
   t.smax = k_t3d[id][4] * 1024 / (fp64 ? 8 : 4);
-  // a one-row box: 3 rows x (cols + 8) x (tz + 2) planes + 3 column tables
-  const int cmax = ((t.smax / (3 * (t.tz + 2) + 3)) - 8) & ~3;
+  // a one-row box: 3 rows x (cols + 8) x (tz + 2) planes + 5 column tables
+  const int cmax = ((t.smax / (3 * (t.tz + 2) + 5)) - 8) & ~3;
   t.cols = cmax < 1024 ? cmax : 1024;
   return t;
 }
@@ -1987,14 +1987,14 @@ static const void* sweep_fn(int dim, int id, int* nthreads, int* dyn) {
     PMA_T2D(E)
 #undef E
   } else {
-#define E(a, b, c, d, e)                                                   \
+#define E(a, b, c, d, e, m)                                                \
   if (k++ == id) {                                                         \
     *nthreads = (a);                                                       \
     *dyn = (e) * 1024;                                                     \
     if constexpr (sizeof(T) == 8)                                          \
-      return (const void*)k_band3d<T, a, d>;                               \
+      return (const void*)k_band3d<T, a, d, 2>;                            \
     else                                                                   \
-      return (const void*)k_band3d<T, a, c>;                               \
+      return (const void*)k_band3d<T, a, c, m>;                            \
   }
     PMA_T3D(E)
 #undef E
