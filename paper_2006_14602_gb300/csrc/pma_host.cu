@@ -596,11 +596,13 @@ void push_items(const HostSub& hs, int dim, bool fp64, int tile_id, int sidx, in
 
 // Neighbour entries of the subdomains subs[0..n) of one problem (blocks in
 // raster order over parts), appended to `out` (see NbEnt).
-void fill_nb(const SubDesc* subs, int n, const int parts[3], int esize, std::vector<NbEnt>& out) {
+void fill_nb(const SubDesc* subs, int n, int dim, const int parts[3], int esize,
+             std::vector<NbEnt>& out) {
+  const int per = dim == 3 ? 27 : 9;
   for (int s = 0; s < n; ++s) {
     const SubDesc& me = subs[s];
-    for (int q = 0; q < kNbPerSub; ++q) {
-      const int d[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+    for (int q = 0; q < per; ++q) {
+      const int d[3] = {q % 3 - 1, (q / 3) % 3 - 1, per == 27 ? q / 9 - 1 : 0};
       int k[3];
       bool ok = true;
       for (int a = 0; a < 3; ++a) {
@@ -667,13 +669,17 @@ pma_status rebuild(pma_ctx* c) {
       c->h_subs.push_back(sd);
     }
     pd.tile_end = (int)wl.size();
-    fill_nb(c->h_subs.data() + pd.sub_base, (int)r.subs.size(), pd.parts, r.esize, c->h_nb);
+    const int nb_base = (int)c->h_nb.size();
+    fill_nb(c->h_subs.data() + pd.sub_base, (int)r.subs.size(), r.dim, pd.parts, r.esize,
+            c->h_nb);
     if (live) {
       c->live_tiles += pd.tile_end - pd.tile_begin;
       c->h_fin[r.cls].push_back(r.slot);
     }
     fill_hot<float>(r, pd, c->h_hotf[r.slot]);
     fill_hot<double>(r, pd, c->h_hotd[r.slot]);
+    c->h_hotf[r.slot].nb_base = nb_base;
+    c->h_hotd[r.slot].nb_base = nb_base;
   }
   pma_status st;
   if ((st = ensure_buf(&c->d_subs, &c->subs_cap, c->h_subs.size() + 1)) != PMA_OK) return st;
@@ -1796,7 +1802,7 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   // scratch layout; everything must fit the fixed array
   Carve cv;
   const size_t o_subs = cv.take(sizeof(SubDesc) * subs.size());
-  const size_t o_nb = cv.take(sizeof(NbEnt) * kNbPerSub * subs.size());
+  const size_t o_nb = cv.take(sizeof(NbEnt) * 27 * subs.size());
   const size_t o_work = cv.take(sizeof(WorkItem) * work.size());
   const size_t o_part = cv.take(sizeof(Partial) * work.size());
   const size_t o_prob = cv.take(sizeof(ProbDesc));
@@ -1823,7 +1829,7 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   ProbDesc pd;
   fill_probdesc(r, pd);
   std::vector<NbEnt> nb;
-  fill_nb(subs.data(), (int)subs.size(), pd.parts, r.esize, nb);
+  fill_nb(subs.data(), (int)subs.size(), r.dim, pd.parts, r.esize, nb);
   pd.sub_base = 0;
   pd.tile_begin = 0;
   pd.tile_end = (int)work.size();

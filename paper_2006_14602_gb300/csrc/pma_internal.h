@@ -66,7 +66,8 @@ struct alignas(16) ProbHot {
   int parts[3], ntiles;
   int alternating;  // 1: alternating transmission (Algorithm 1)
   int mon_fast;     // 1: sum of bump / ring terms (the packed monitor path)
-  int pad1[2];
+  int nb_base;      // first neighbour entry of the problem's subdomains
+  int pad1;
   T lo[3], h[3], inv2h[3], invh2[3], inv4hh[3], hw[3];
   T dt, vol;
   double hd[3];
@@ -212,17 +213,17 @@ cudaError_t launch_res2d(bool fp64, int id, const ResArgs& a, int nclusters, int
                          int smem_bytes, cudaStream_t s);
 
 // Kernel launch entry points (pma_kernels.cu).
-// Owners of transmission nodes: for every subdomain, kNbPerSub entries, one
-// per block offset (dx, dy, dz) in {-1, 0, 1}^3 (entry 13 + dx + 3 dy + 9 dz):
-// the neighbouring block's two state buffers, shifted so that the owner's
-// value at local node (i, j, l) of THIS subdomain is element
-// i + pitch j + plane l of v[parity]; null where there is no such block.
+// Owners of transmission nodes: for every subdomain, 3^dim entries, one per
+// block offset (dx, dy[, dz]) in {-1, 0, 1}^dim (entry (dx + 1) + 3 (dy + 1)
+// [+ 9 (dz + 1)]): the neighbouring block's two state buffers, shifted so
+// that the owner's value at local node (i, j, l) of THIS subdomain is
+// element i + pitch j + plane l of v[parity]; null where there is no such
+// block.  A problem's entries start at ProbHot::nb_base.
 struct alignas(16) NbEnt {
   const void* v[2];
   int pitch, plane;
   long long pad;
 };
-constexpr int kNbPerSub = 27;
 static_assert(sizeof(NbEnt) == 32, "neighbour entry is 32 bytes");
 
 struct LaunchArgs {
@@ -232,7 +233,7 @@ struct LaunchArgs {
   int t0;                // first work item of this launch
   int nwork;             // work items of this launch
   const SubDesc* subs;
-  const NbEnt* nb;       // kNbPerSub entries per subdomain
+  const NbEnt* nb;       // neighbour entries (3^dim per subdomain)
   const ProbDesc* probs;
   ProbState* st;
   Partial* part;

@@ -265,6 +265,10 @@ __global__ void k_finish(const int* __restrict__ list, int n, const SubDesc* __r
   gn = warp_min(gn);
   dm = warp_min(dm);
   nf = warp_isum(nf);
+  // the rest is scalar (one lane) unless the residual needs per-subdomain
+  // folds by the whole warp
+  const bool per_sub = pd.stop_norm != PMA_STOP_MAX_UT || pd.stop_rule == PMA_RULE_ANY;
+  if (lane != 0 && (phase == PH_INIT_THETA || !per_sub)) return;
   const double theta = th;
   double c_n = 0.0;
   if (pd.rhs == PMA_RHS_LOG && pd.normalize == PMA_NORM_GLOBAL_THETA) c_n = log(theta / pd.vol);
@@ -276,7 +280,7 @@ __global__ void k_finish(const int* __restrict__ list, int n, const SubDesc* __r
   // residual: per subdomain, combined by the stop rule (max = ALL, min = ANY)
   const bool any = (pd.stop_rule == PMA_RULE_ANY);
   double r;
-  if (pd.stop_norm == PMA_STOP_MAX_UT && !any) {
+  if (!per_sub) {
     r = fmax(gx - c_n, c_n - gn);
   } else {
     const double delta = c_n - c_lag;
@@ -328,14 +332,20 @@ cudaError_t launch_finish(const int* list, int n, const SubDesc* subs, const Pro
 // transmission: previous step), through the subdomain's neighbour table.  A
 // node outside this subdomain's core along an axis belongs to the
 // neighbouring block on that side (cores hold >= ceil(o/2)+1 nodes).
-template <typename T>
-__device__ __forceinline__ T gather_owner(const LaunchArgs& a, const SmemHdr<T>& S, int i, int j,
+// The item's first neighbour entry (3^D per subdomain).
+template <typename T, int D>
+__device__ __forceinline__ const NbEnt* item_nb(const LaunchArgs& a, const SmemHdr<T>& S) {
+  return a.nb + S.ph.nb_base + (S.w.sub - S.ph.sub_base) * (D == 3 ? 27 : 9);
+}
+template <typename T, int D>
+__device__ __forceinline__ T gather_owner(const NbEnt* nbi, const SmemHdr<T>& S, int i, int j,
                                           int l) {
   const int qx = i < S.sd.clo[0] ? 0 : (i > S.sd.chi[0] ? 2 : 1);
   const int qy = j < S.sd.clo[1] ? 0 : (j > S.sd.chi[1] ? 2 : 1);
-  const int qz = l < S.sd.clo[2] ? 0 : (l > S.sd.chi[2] ? 2 : 1);
-  const NbEnt* e = a.nb + S.w.sub * kNbPerSub + qx + 3 * qy + 9 * qz;
+  const int qz = D == 3 ? (l < S.sd.clo[2] ? 0 : (l > S.sd.chi[2] ? 2 : 1)) : 0;
+  const NbEnt* e = nbi + qx + 3 * qy + 9 * qz;
   const T* ov = (const T*)__ldg((const unsigned long long*)&e->v[S.ps.parity]);
+  if (ov == nullptr) return T(0);  // no such block: never a transmission node's owner
   const int2 pp = __ldg((const int2*)&e->pitch);
   return __ldcg(ov + i + (long long)pp.x * j + (long long)pp.y * l);
 }
@@ -903,6 +913,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
         const int ncl = (ic0 >= 0 ? 1 : 0) + (ic1 >= 0 ? 1 : 0);
         const int nrow_e = nrw * cols;
         const int total = nrow_e + ncl * rows;
+        const NbEnt* const nbi = item_nb<T, 2>(a, H);
         for (int e = tid; e < total; e += NT) {
           int i, j;
           if (e < nrow_e) {
@@ -916,7 +927,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
             j = j0 + e2 - q * rows;
             if (j == jr0 || j == jr1) continue;  // corner: done with its row
           }
-          st_global(dst + j * pitch + i, gather_owner<T>(a, H, i, j, 0));
+          st_global(dst + j * pitch + i, gather_owner<T, 2>(nbi, H, i, j, 0));
         }
       }
       // (b) halo columns on the subdomain's x faces (Neumann mirror; clamp on
@@ -1588,6 +1599,7 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
         const int ncl = (ic0 >= 0 ? 1 : 0) + (ic1 >= 0 ? 1 : 0);
         const int plane_e = rows * cols, nrow_e = nrw * cols, per_plane = nrow_e + ncl * rows;
         const int total = npl * plane_e + depth * per_plane;
+        const NbEnt* const nbi = item_nb<T, 3>(a, H);
         for (int e = tid; e < total; e += NT) {
           int i, j, kk;
           if (e < npl * plane_e) {
@@ -1612,7 +1624,7 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
               if (j == jr0 || j == jr1) continue;  // corner: done with its row
             }
           }
-          st_global(dst + kk * ppitch + j * pitch + i, gather_owner<T>(a, H, i, j, kk));
+          st_global(dst + kk * ppitch + j * pitch + i, gather_owner<T, 3>(nbi, H, i, j, kk));
         }
       }
       // (b) x-halo columns (Neumann mirror; clamp on transmission faces)
