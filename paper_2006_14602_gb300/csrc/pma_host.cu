@@ -512,6 +512,20 @@ void fill_hot(const Request& r, const ProbDesc& pd, ProbHot<T>& h) {
     o.k2 = (T)(2.0 * q.k);
     for (int a = 0; a < 3; ++a) o.c[a] = (T)q.c[a];
   }
+  h.mon.nring = 0;
+  if (h.mon_fast) {
+    // rings first, then bumps (the sweep evaluates the two kinds in two
+    // branch-free loops); the sum is the same up to rounding order
+    typename MonT<T>::Term sorted[kMaxTerms];
+    int n = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int t = 0; t < r.m.nterms && t < kMaxTerms; ++t)
+        if ((h.mon.t[t].type == PMA_TERM_RING) == (pass == 0)) sorted[n++] = h.mon.t[t];
+    for (int t = 0; t < n; ++t) {
+      h.mon.t[t] = sorted[t];
+      if (sorted[t].type == PMA_TERM_RING) h.mon.nring = t + 1;
+    }
+  }
 }
 
 int pick_tile(pma_ctx* c, int cls) {

@@ -43,7 +43,9 @@ struct MonDev {
 // sin(2 pi k s) = sinpi(k2 s).
 template <typename T>
 struct alignas(16) MonT {
-  int kind, nterms, dim, pad;
+  int kind, nterms, dim;
+  int nring;  // sum of bumps / rings: the terms are stored rings first
+              // (nring of them), then bumps; 0 for the other kinds
   T base, p0;
   struct Term {
     int type, axis, along, pad;

@@ -614,6 +614,41 @@ __device__ __forceinline__ void load_row6(const T* p, T* w) {
   w[5] = p[4];
 }
 
+// One Gaussian ring (RING) or bump term of the monitor sum at two pairs of
+// nodes: amp exp(-width u) with u = ((x - c)^2 - r^2)^2 or (x - c)^2.
+template <typename T, bool RING>
+__device__ __forceinline__ void sum_terms2(const typename MonT<T>::Term& tm, const P2<T>* X0,
+                                           const P2<T>* X1, P2<T>* R) {
+  const P2<T> CX = P2<T>::s(tm.c[0]), CY = P2<T>::s(tm.c[1]);
+  const P2<T> NWd = P2<T>::s(-tm.width), AMP = P2<T>::s(tm.amp);
+#pragma unroll
+  for (int pp = 0; pp < 2; ++pp) {
+    const P2<T> d0 = psub(X0[pp], CX), d1 = psub(X1[pp], CY);
+    P2<T> uu = pfma(d0, d0, pmul(d1, d1));
+    if (RING) {
+      const P2<T> s2 = psub(uu, P2<T>::s(tm.r2));
+      uu = pmul(s2, s2);
+    }
+    R[pp] = pfma(AMP, pexw<T>(pmul(uu, NWd)), R[pp]);
+  }
+}
+template <typename T, bool RING>
+__device__ __forceinline__ void sum_terms3(const typename MonT<T>::Term& tm, const P2<T>* X0,
+                                           const P2<T>* X1, const P2<T>* X2, P2<T>* R) {
+  const P2<T> CX = P2<T>::s(tm.c[0]), CY = P2<T>::s(tm.c[1]), CZ = P2<T>::s(tm.c[2]);
+  const P2<T> NWd = P2<T>::s(-tm.width), AMP = P2<T>::s(tm.amp);
+#pragma unroll
+  for (int pp = 0; pp < 2; ++pp) {
+    const P2<T> d0 = psub(X0[pp], CX), d1 = psub(X1[pp], CY), d2 = psub(X2[pp], CZ);
+    P2<T> uu = pfma(d0, d0, pfma(d1, d1, pmul(d2, d2)));
+    if (RING) {
+      const P2<T> s2 = psub(uu, P2<T>::s(tm.r2));
+      uu = pmul(s2, s2);
+    }
+    R[pp] = pfma(AMP, pexw<T>(pmul(uu, NWd)), R[pp]);
+  }
+}
+
 // Column tables of a staged band or subdomain, at the run's first column:
 // theta weight (owned columns, else 0), 1 at updated columns (else 0), the
 // local trapezoid weight, and with TAB the node's xi_x and +big at columns
@@ -676,23 +711,11 @@ __device__ __forceinline__ void stencil_core4(const RunK<T>& K, const MonT<T>& m
     DD[pp] = pfma(pmul(df, K.INV4), pmul(df, K.NINV4), pmul(hxx, hyy));
   }
   if (K.fast) {
-    // sum of Gaussian bumps / rings, two nodes per operation
+    // sum of Gaussian rings, then bumps, two nodes per operation
 #pragma unroll
     for (int pp = 0; pp < 2; ++pp) R[pp] = P2<T>::s(mon.base);
-    for (int k = 0; k < K.nterms; ++k) {
-      const auto& tm = mon.t[k];
-      const P2<T> CX = P2<T>::s(tm.c[0]), CY = P2<T>::s(tm.c[1]), R2 = P2<T>::s(tm.r2);
-      const P2<T> NWd = P2<T>::s(-tm.width), AMP = P2<T>::s(tm.amp);
-      const bool ring = tm.type == PMA_TERM_RING;
-#pragma unroll
-      for (int pp = 0; pp < 2; ++pp) {
-        const P2<T> d0 = psub(X0[pp], CX), d1 = psub(X1[pp], CY);
-        const P2<T> qq = pfma(d0, d0, pmul(d1, d1));
-        const P2<T> s2 = psub(qq, R2);
-        const P2<T> uu = ring ? pmul(s2, s2) : qq;
-        R[pp] = pfma(AMP, pexw<T>(pmul(uu, NWd)), R[pp]);
-      }
-    }
+    for (int k = 0; k < mon.nring; ++k) sum_terms2<T, true>(mon.t[k], X0, X1, R);
+    for (int k = mon.nring; k < K.nterms; ++k) sum_terms2<T, false>(mon.t[k], X0, X1, R);
   } else {
 #pragma unroll
     for (int pp = 0; pp < 2; ++pp)
@@ -1800,20 +1823,10 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
           if (fast) {
 #pragma unroll
             for (int pp = 0; pp < 2; ++pp) R[pp] = P2<T>::s(H.ph.mon.base);
-            for (int k = 0; k < nterms; ++k) {
-              const auto& tm = H.ph.mon.t[k];
-              const P2<T> CX = P2<T>::s(tm.c[0]), CY = P2<T>::s(tm.c[1]), CZ = P2<T>::s(tm.c[2]);
-              const P2<T> R2 = P2<T>::s(tm.r2), NWd = P2<T>::s(-tm.width), AMP = P2<T>::s(tm.amp);
-              const bool ring = tm.type == PMA_TERM_RING;
-#pragma unroll
-              for (int pp = 0; pp < 2; ++pp) {
-                const P2<T> d0 = psub(X0[pp], CX), d1 = psub(X1[pp], CY), d2 = psub(X2[pp], CZ);
-                const P2<T> qq = pfma(d0, d0, pfma(d1, d1, pmul(d2, d2)));
-                const P2<T> s2 = psub(qq, R2);
-                const P2<T> uu = ring ? pmul(s2, s2) : qq;
-                R[pp] = pfma(AMP, pexw<T>(pmul(uu, NWd)), R[pp]);
-              }
-            }
+            const int nring = H.ph.mon.nring;
+            for (int k = 0; k < nring; ++k) sum_terms3<T, true>(H.ph.mon.t[k], X0, X1, X2, R);
+            for (int k = nring; k < nterms; ++k)
+              sum_terms3<T, false>(H.ph.mon.t[k], X0, X1, X2, R);
           } else {
 #pragma unroll
             for (int pp = 0; pp < 2; ++pp)
