@@ -254,6 +254,55 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Tensor-memory-access (TMA) copies into shared memory, completed on an
+// mbarrier: the issuing thread announces the bytes (expect_tx) and issues
+// the copy; every thread then waits on the barrier's phase.
+__device__ __forceinline__ unsigned int smem_u32(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Orders this thread's (and, after a barrier, the block's) earlier generic
+// shared-memory accesses before later asynchronous-proxy writes.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// 2D tiled copy of the box at (x, y) (x a multiple of 16 bytes of elements;
+// coordinates outside the tensor read zeros).
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// Wait until the barrier's phase with parity `phase` has completed, for at
+// most about a second of SM clock; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int phase) {
+  const unsigned int a = smem_u32(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned int ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(a), "r"(phase)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
 // Thread-block clusters: rank, size, barrier (release / acquire), and loads
 // from another CTA's shared memory through the shared::cluster window.
 __device__ __forceinline__ unsigned int cluster_rank() {

@@ -9,6 +9,7 @@
 // per-problem scalars, retires finished requests, admits queued ones while
 // the memory budget allows (continuous batching), and rebuilds the tables
 // when the set of requests changed.
+#include <cuda.h>  // CUtensorMap and its encoder's types (called through the runtime's entry point)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -293,6 +294,8 @@ struct pma_ctx {
   SubDesc* d_subs = nullptr;
   NbEnt* d_nb = nullptr;
   size_t nb_cap = 0;
+  CUtensorMap* d_tmap = nullptr;  // two per subdomain (2D bands staged by TMA)
+  size_t tmap_cap = 0;
   size_t subs_cap = 0;
   WorkItem* d_work[NUM_CLS] = {};
   Partial* d_part[NUM_CLS] = {};
@@ -302,11 +305,13 @@ struct pma_ctx {
   size_t fin_cap[NUM_CLS] = {};
   int nfin[NUM_CLS] = {};
   std::vector<int> h_fin[NUM_CLS];
-  unsigned int* d_queue = nullptr;  // 2 counters per class
+  unsigned int* d_queue = nullptr;  // 2 counters per class, then the error word
   int grid[NUM_CLS] = {};
   int tile_id[NUM_CLS] = {};
   std::vector<SubDesc> h_subs;
   std::vector<NbEnt> h_nb;
+  std::vector<CUtensorMap> h_tmap;
+  unsigned int h_err = 0;
   std::vector<WorkItem> h_work[NUM_CLS];
   bool dirty = true;
   long long dead_tiles = 0, live_tiles = 0;
@@ -580,10 +585,13 @@ void push_items(const HostSub& hs, int dim, bool fp64, int tile_id, int sidx, in
       int rows = std::max(1, std::min(hs.n[1], t2.nodes / cr));
       while (rows > 1 && ((rows + 2) * swp + 5 * cr > t2.smax || rows + 2 > 2 * t2.threads))
         --rows;
+      // one TMA box per band where the subdomain is one strip and the box
+      // fits the copy engine's 256 x 256 limit
+      const int tr = (cols == hs.n[0] && swp <= 256 && rows + 2 <= 256) ? rows + 2 : 0;
       for (int y = 0; y < hs.n[1]; y += rows) {
         const int rr = std::min(rows, hs.n[1] - y);
         wl.push_back(WorkItem{sidx, slot, x | (y << 16), cols | (rr << 16), 0,
-                              band_flags(hs, x, y, cols, rr), {0, 0}});
+                              band_flags(hs, x, y, cols, rr), tr, 0});
       }
     }
   } else {
@@ -601,11 +609,52 @@ void push_items(const HostSub& hs, int dim, bool fp64, int tile_id, int sidx, in
         for (int z = 0; z < hs.n[2]; z += t3.tz) {
           const int d = std::min(t3.tz, hs.n[2] - z);
           wl.push_back(WorkItem{sidx, slot, x | (y << 16), cols | (rr << 16), z | (d << 16), 0,
-                                {0, 0}});
+                                0, 0});
         }
       }
     }
   }
+}
+
+// The driver's tiled tensor-map encoder, found once through the runtime
+// (no link-time dependency on the driver library); null if unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+// Tensor maps of a 2D subdomain's two state buffers for the TMA staging of
+// its bands: the buffer as a (pitch x n1) array of rows, boxes of
+// (SWp x box_rows) elements, zero fill outside.  Returns false (the bands
+// then stage with cp.async) if the encoder is missing or refuses.
+bool encode_band_maps(const SubDesc& sd, int esize, int cols, int box_rows, CUtensorMap out[2]) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)sd.pitch, (cuuint64_t)sd.n[1]};
+  const cuuint64_t strides[1] = {(cuuint64_t)sd.pitch * (cuuint64_t)esize};
+  const cuuint32_t box[2] = {(cuuint32_t)(((cols + 3) & ~3) + 8), (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  for (int p = 0; p < 2; ++p) {
+    if (fn(&out[p], esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+           2, sd.v[p], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
 }
 
 // Neighbour entries of the subdomains subs[0..n) of one problem (blocks in
@@ -643,6 +692,7 @@ void fill_nb(const SubDesc* subs, int n, int dim, const int parts[3], int esize,
 pma_status rebuild(pma_ctx* c) {
   c->h_subs.clear();
   c->h_nb.clear();
+  c->h_tmap.clear();
   for (int k = 0; k < NUM_CLS; ++k) {
     c->h_work[k].clear();
     c->h_fin[k].clear();
@@ -680,6 +730,11 @@ pma_status rebuild(pma_ctx* c) {
       if (live)
         push_items(hs, r.dim, r.esize == 8, c->tile_id[r.cls], (int)c->h_subs.size(), r.slot, wl);
       sd.tile_end = (int)wl.size();
+      c->h_tmap.resize(2 * (c->h_subs.size() + 1));
+      if (sd.tile_end > sd.tile_begin && wl[sd.tile_begin].tma_rows > 0 &&
+          !encode_band_maps(sd, r.esize, hs.n[0], wl[sd.tile_begin].tma_rows,
+                            &c->h_tmap[2 * c->h_subs.size()]))
+        for (int t = sd.tile_begin; t < sd.tile_end; ++t) wl[t].tma_rows = 0;
       c->h_subs.push_back(sd);
     }
     pd.tile_end = (int)wl.size();
@@ -698,10 +753,13 @@ pma_status rebuild(pma_ctx* c) {
   pma_status st;
   if ((st = ensure_buf(&c->d_subs, &c->subs_cap, c->h_subs.size() + 1)) != PMA_OK) return st;
   if ((st = ensure_buf(&c->d_nb, &c->nb_cap, c->h_nb.size() + 1)) != PMA_OK) return st;
+  if ((st = ensure_buf(&c->d_tmap, &c->tmap_cap, c->h_tmap.size() + 2)) != PMA_OK) return st;
   if (!c->h_subs.empty()) {
     PMA_CK(cudaMemcpyAsync(c->d_subs, c->h_subs.data(), sizeof(SubDesc) * c->h_subs.size(),
                            cudaMemcpyHostToDevice, c->stream));
     PMA_CK(cudaMemcpyAsync(c->d_nb, c->h_nb.data(), sizeof(NbEnt) * c->h_nb.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+    PMA_CK(cudaMemcpyAsync(c->d_tmap, c->h_tmap.data(), sizeof(CUtensorMap) * c->h_tmap.size(),
                            cudaMemcpyHostToDevice, c->stream));
   }
   for (int k = 0; k < NUM_CLS; ++k) {
@@ -734,6 +792,7 @@ pma_status rebuild(pma_ctx* c) {
   PMA_CK(cudaMemcpyAsync(c->d_hotd, c->h_hotd.data(), sizeof(ProbHot<double>) * c->slot_cap,
                          cudaMemcpyHostToDevice, c->stream));
   c->stats.h2d_bytes += (double)(sizeof(SubDesc) * c->h_subs.size() + sizeof(NbEnt) * c->h_nb.size() +
+                                 sizeof(CUtensorMap) * c->h_tmap.size() +
                                  (sizeof(ProbDesc) + sizeof(ProbHot<float>) +
                                   sizeof(ProbHot<double>)) * c->slot_cap);
   for (int k = 0; k < NUM_CLS; ++k) c->stats.h2d_bytes += (double)sizeof(WorkItem) * c->nwork[k];
@@ -883,6 +942,8 @@ LaunchArgs args_for(pma_ctx* c, int k, int t0, int n) {
   a.nwork = n;
   a.subs = c->d_subs;
   a.nb = c->d_nb;
+  a.tmap = c->d_tmap;
+  a.err = c->d_queue + 2 * NUM_CLS;
   a.probs = c->d_probs;
   a.st = c->d_state;
   a.part = c->d_part[k];
@@ -1022,7 +1083,13 @@ pma_status run_window(pma_ctx* c, int steps) {
   PMA_CK(cudaEventRecord(c->ev1, c->stream));
   PMA_CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(ProbState) * c->slot_cap,
                          cudaMemcpyDeviceToHost, c->stream));
+  PMA_CK(cudaMemcpyAsync(&c->h_err, c->d_queue + 2 * NUM_CLS, sizeof(unsigned int),
+                         cudaMemcpyDeviceToHost, c->stream));
   PMA_CK(cudaStreamSynchronize(c->stream));
+  if (c->h_err != 0) {
+    set_err("a sweep kernel gave up waiting for its staging copies (bounded wait)");
+    return PMA_ERR_TIMEOUT;
+  }
   float ms = 0.f;
   PMA_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   c->stats.windows += 1;
@@ -1257,8 +1324,8 @@ pma_status pma_create(pma_ctx** out, int device, size_t mem_budget_bytes, void* 
   pma_status st = ensure_slots(c.get(), 64);
   if (st != PMA_OK) return st;
   PMA_CK(cudaMalloc(&c->d_check, sizeof(double) * 4 + sizeof(unsigned long long)));
-  PMA_CK(cudaMalloc(&c->d_queue, sizeof(unsigned int) * 2 * NUM_CLS));
-  PMA_CK(cudaMemset(c->d_queue, 0, sizeof(unsigned int) * 2 * NUM_CLS));
+  PMA_CK(cudaMalloc(&c->d_queue, sizeof(unsigned int) * (2 * NUM_CLS + 1)));
+  PMA_CK(cudaMemset(c->d_queue, 0, sizeof(unsigned int) * (2 * NUM_CLS + 1)));
   PMA_CK(cudaEventCreate(&c->ev0));
   PMA_CK(cudaEventCreate(&c->ev1));
   *out = c.release();
@@ -1281,6 +1348,7 @@ pma_status pma_destroy(pma_ctx* c) {
   cudaFreeHost(c->h_state);
   cudaFree(c->d_subs);
   cudaFree(c->d_nb);
+  cudaFree(c->d_tmap);
   for (int k = 0; k < NUM_CLS; ++k) {
     cudaFree(c->d_work[k]);
     cudaFree(c->d_part[k]);
@@ -1812,6 +1880,7 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
     sd.tile_end = (int)work.size();
     subs.push_back(sd);
   }
+  for (WorkItem& w : work) w.tma_rows = 0;  // the static path stages with cp.async
 
   // scratch layout; everything must fit the fixed array
   Carve cv;
@@ -1823,7 +1892,7 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   const size_t o_hotf = cv.take(sizeof(ProbHot<float>));
   const size_t o_hotd = cv.take(sizeof(ProbHot<double>));
   const size_t o_st = cv.take(sizeof(ProbState));
-  const size_t o_q = cv.take(sizeof(unsigned int) * 2 * NUM_CLS);
+  const size_t o_q = cv.take(sizeof(unsigned int) * (2 * NUM_CLS + 1));
   const size_t o_fin = cv.take(sizeof(int));
   const size_t o_job = cv.take(sizeof(CombineJob));
   const size_t o_v = cv.take(r.bytes);
@@ -1872,7 +1941,7 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
     PMA_CK(cudaMemcpyAsync(r.block + r.tab_off, r.tab_dev.data(), r.tab_dev.size(),
                            cudaMemcpyHostToDevice, s));
   PMA_CK(cudaMemcpyAsync(B + o_fin, &fin, sizeof(fin), cudaMemcpyHostToDevice, s));
-  PMA_CK(cudaMemsetAsync(B + o_q, 0, sizeof(unsigned int) * 2 * NUM_CLS, s));
+  PMA_CK(cudaMemsetAsync(B + o_q, 0, sizeof(unsigned int) * (2 * NUM_CLS + 1), s));
   PMA_CK(cudaStreamSynchronize(s));
 
   int num_sms = 1;
@@ -1886,6 +1955,8 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   la.nwork = (int)work.size();
   la.subs = (const SubDesc*)(B + o_subs);
   la.nb = (const NbEnt*)(B + o_nb);
+  la.tmap = nullptr;
+  la.err = (unsigned int*)(B + o_q) + 2 * NUM_CLS;
   la.probs = (const ProbDesc*)(B + o_prob);
   la.st = (ProbState*)(B + o_st);
   la.part = (Partial*)(B + o_part);

@@ -140,7 +140,10 @@ struct alignas(16) WorkItem {
   // row (each row flagged once); bit 4 / 5 = staged column 4 / cols + 3
   // (local column 0 / n0 - 1) is a transmission column.  3D: 0.
   int flags;
-  int pad[2];
+  // 2D: rows of the band's TMA box (the subdomain's full bands plus the
+  // halo rows; the box is SWp columns wide), 0 = staged by cp.async
+  int tma_rows;
+  int pad;
 };
 
 struct Partial {
@@ -236,6 +239,8 @@ struct LaunchArgs {
   int nwork;             // work items of this launch
   const SubDesc* subs;
   const NbEnt* nb;       // neighbour entries (3^dim per subdomain)
+  const void* tmap;      // 2D: two tensor maps (128 B each) per subdomain, by parity
+  unsigned int* err;     // device error word (bit 0: a bounded wait gave up)
   const ProbDesc* probs;
   ProbState* st;
   Partial* part;

@@ -805,8 +805,9 @@ template <typename T, int NT, int SMAX>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2d(LaunchArgs a) {
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int NW = NT / 32;
-  __shared__ __align__(16) T sv[SMAX];
+  __shared__ __align__(128) T sv[SMAX];
   __shared__ __align__(16) BandHdr<T> HB[2];
+  __shared__ __align__(8) unsigned long long tbar;  // TMA staging barrier
   __shared__ int s_t[2];
   __shared__ T red_t[4 * NW];
   __shared__ T red_f[3 * NW];
@@ -815,6 +816,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
   const int tend = a.t0 + a.nwork;
   int t_next = 0;
   WorkItem w_next;
+  unsigned int tph = 0;  // parity of the TMA barrier's next phase
+  if (tid == 0) mbar_init(&tbar, 1);
+  __syncthreads();
   if (tid == 0) {
     const int t0 = pull_item(a);
     s_t[0] = t0;
@@ -884,17 +888,31 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
     } else {
       const int SWp = ((cols + 3) & ~3) + 8;
       const int SH = rows + 2;
+      const int tr = a.tmap != nullptr ? H.w.tma_rows : 0;
       const int cpr = SWp / VW;  // 16-byte chunks per shared row
       const float inv_cpr = __fdividef(1.0f, (float)cpr);
       const bool plx = faces & 1, phx = faces & 2, ply = faces & 4, phy = faces & 8;
-      // (a) 16-byte asynchronous copies of the band rows (global columns
-      //     i0-4 .. i0+SWp-5; chunks outside the pitched row are skipped)
-      for (int e = tid; e < SH * cpr; e += NT) {
-        const int r = qdiv(e, cpr, inv_cpr), k = e - r * cpr;
-        const int gs = i0 - 4 + k * VW;
-        if (gs >= 0 && gs + VW <= pitch) {
-          const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
-          cp_async16(sv + r * SWp + k * VW, src + jj * pitch + gs);
+      // (a) the band rows (global columns i0-4 .. i0+SWp-5, rows j0-1 ..
+      //     j0+rows): one TMA box where the subdomain has tensor maps (the
+      //     box holds SHT >= SH rows; zeros outside the buffer, mirror rows
+      //     fixed below), else 16-byte asynchronous copies (chunks outside
+      //     the pitched row skipped, rows mirrored / clamped).
+      const int SHT = tr > 0 ? tr : SH;
+      if (tr > 0) {
+        if (tid == 0) {
+          fence_proxy_async();
+          mbar_expect_tx(&tbar, (unsigned int)(SWp * tr * (int)sizeof(T)));
+          tma_load_2d(sv, (const char*)a.tmap + 128 * (2 * (size_t)H.w.sub + H.ps.parity),
+                      i0 - 4, j0 - 1, &tbar);
+        }
+      } else {
+        for (int e = tid; e < SH * cpr; e += NT) {
+          const int r = qdiv(e, cpr, inv_cpr), k = e - r * cpr;
+          const int gs = i0 - 4 + k * VW;
+          if (gs >= 0 && gs + VW <= pitch) {
+            const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
+            cp_async16(sv + r * SWp + k * VW, src + jj * pitch + gs);
+          }
         }
       }
       cp_async_commit();
@@ -907,7 +925,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
       {
       const T h0 = H.ph.h[0], hw0 = H.ph.hw[0], lo0 = H.ph.lo[0];
       const int N0 = H.ph.N[0], clo0 = H.sd.clo[0], chi0 = H.sd.chi[0];
-      T* const wcol = sv + SH * SWp;
+      T* const wcol = sv + SHT * SWp;
       T* const ucol = wcol + cr;
       T* const lcol = ucol + cr;
       T* const xcol = lcol + cr;
@@ -971,7 +989,31 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
         }
       }
       cp_async_wait_all();
-      __syncthreads();
+      bool gave_up = false;
+      if (tr > 0) {
+        gave_up = !mbar_wait(&tbar, tph);
+        tph ^= 1;
+      }
+      if (__syncthreads_or(gave_up)) {
+        // the box never arrived: report, give the copy one more bounded
+        // wait, and leave (the host turns the error word into a status)
+        if (tid == 0) {
+          atomicOr(a.err, 1u);
+          mbar_wait(&tbar, tph ^ 1);
+        }
+        break;
+      }
+      if (tr > 0 && ((ply && j0 == 0) || (phy && j0 + rows == n1))) {
+        // Neumann mirror rows of a TMA box (zeros outside the buffer):
+        // staged row 0 <- row 2, row rows+1 <- row rows-1 (halo columns
+        // are written by (c))
+        for (int c = tid; c < SWp; c += NT) {
+          if ((left && c == 3) || (right && c == cols + 4)) continue;
+          if (ply && j0 == 0) sv[c] = sv[2 * SWp + c];
+          if (phy && j0 + rows == n1) sv[(rows + 1) * SWp + c] = sv[(rows - 1) * SWp + c];
+        }
+        __syncthreads();
+      }
       // (c) halo values, and the offset of transmission nodes (only the band's
       //     perimeter can hold them): whole rows whose global row is a
       //     transmission row (halo columns excluded: written by (b)), and the
@@ -1018,7 +1060,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
       const int N0 = H.ph.N[0], N1 = H.ph.N[1];
       const int clo0 = H.sd.clo[0], chi0 = H.sd.chi[0], clo1 = H.sd.clo[1], chi1 = H.sd.chi[1];
       const bool run = phase == PH_RUN;
-      const T* const wcol = sv + SH * SWp;
+      const T* const wcol = sv + SHT * SWp;
       const T* const ucol = wcol + cr;
       const T* const lcol = ucol + cr;
       const T* const xcol = lcol + cr;
