@@ -916,6 +916,24 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
         }
       }
       cp_async_commit();
+      // (b) halo columns on the subdomain's x faces (Neumann mirror; clamp on
+      //     transmission faces, where the value is never used): loads issued
+      //     now (their latency overlaps the tables and the transmission
+      //     pass), written after the copies land.  At most 2 rows per thread.
+      const bool left = (i0 == 0), right = (i0 + cols == n0);
+      const T corr = (T)H.ps.corr;
+      T hl[2], hr[2], hc[2];  // raw halo values and their offset (added at (c))
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int r = tid + q * NT;
+        hl[q] = hr[q] = hc[q] = T(0);
+        if (r < SH && (left || right)) {
+          const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
+          hc[q] = (jj == dly || jj == dhy) ? corr : T(0);
+          if (left && plx) hl[q] = __ldcg(src + jj * pitch + 1);
+          if (right && phx) hr[q] = __ldcg(src + jj * pitch + n0 - 2);
+        }
+      }
       // Per-column tables of the band (after the staged rows in shared
       // memory): theta weight of owned columns (0 elsewhere), 1 for updated
       // columns (inside the band, not a transmission column), the local
@@ -955,37 +973,34 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
         const int nrow_e = nrw * cols;
         const int total = nrow_e + ncl * rows;
         const NbEnt* const nbi = item_nb<T, 2>(a, H);
-        for (int e = tid; e < total; e += NT) {
-          int i, j;
-          if (e < nrow_e) {
-            const int q = e >= cols ? 1 : 0;
-            j = (q == 0 && jr0 >= 0) ? jr0 : jr1;
-            i = i0 + e - q * cols;
-          } else {
-            const int e2 = e - nrow_e;
-            const int q = e2 >= rows ? 1 : 0;
-            i = (q == 0 && ic0 >= 0) ? ic0 : ic1;
-            j = j0 + e2 - q * rows;
-            if (j == jr0 || j == jr1) continue;  // corner: done with its row
-          }
-          st_global(dst + j * pitch + i, gather_owner<T, 2>(nbi, H, i, j, 0));
-        }
-      }
-      // (b) halo columns on the subdomain's x faces (Neumann mirror; clamp on
-      //     transmission faces, where the value is never used): loaded now,
-      //     written after the copies land.  At most 2 rows per thread.
-      const bool left = (i0 == 0), right = (i0 + cols == n0);
-      const T corr = (T)H.ps.corr;
-      T hl[2], hr[2];
+        for (int e0 = tid; e0 < total; e0 += 2 * NT) {
+          // two nodes per thread and pass: both owner loads before the stores
+          T val[2];
+          T* dp[2];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int r = tid + q * NT;
-        hl[q] = hr[q] = T(0);
-        if (r < SH && (left || right)) {
-          const int jj = reflect_clamp(j0 - 1 + r, n1, ply, phy);
-          const T cr = (jj == dly || jj == dhy) ? corr : T(0);
-          if (left && plx) hl[q] = __ldcg(src + jj * pitch + 1) + cr;
-          if (right && phx) hr[q] = __ldcg(src + jj * pitch + n0 - 2) + cr;
+          for (int u = 0; u < 2; ++u) {
+            const int e = e0 + u * NT;
+            dp[u] = nullptr;
+            val[u] = T(0);
+            if (e >= total) continue;
+            int i, j;
+            if (e < nrow_e) {
+              const int q = e >= cols ? 1 : 0;
+              j = (q == 0 && jr0 >= 0) ? jr0 : jr1;
+              i = i0 + e - q * cols;
+            } else {
+              const int e2 = e - nrow_e;
+              const int q = e2 >= rows ? 1 : 0;
+              i = (q == 0 && ic0 >= 0) ? ic0 : ic1;
+              j = j0 + e2 - q * rows;
+              if (j == jr0 || j == jr1) continue;  // corner: done with its row
+            }
+            dp[u] = dst + j * pitch + i;
+            val[u] = gather_owner<T, 2>(nbi, H, i, j, 0);
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (dp[u]) st_global(dp[u], val[u]);
         }
       }
       cp_async_wait_all();
@@ -1023,8 +1038,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
       for (int q = 0; q < 2; ++q) {
         const int r = tid + q * NT;
         if (r < SH) {
-          if (left) sv[r * SWp + 3] = hl[q];
-          if (right) sv[r * SWp + cols + 4] = hr[q];
+          if (left) sv[r * SWp + 3] = hl[q] + hc[q];
+          if (right) sv[r * SWp + cols + 4] = hr[q] + hc[q];
         }
       }
       const int fl = H.w.flags;
