@@ -229,10 +229,20 @@ pma_status pma_destroy(pma_ctx *ctx);
  *                          a few microseconds against tens for a band step,
  *                          so resident requests can run several band windows'
  *                          worth of steps while the band work of a window
- *                          runs beside them (results do not depend on it). */
+ *                          runs beside them (results do not depend on it).
+ *   PMA_OPT_TEST_STALL     test hook of the bounded waits: 1 = the 2D band
+ *                          kernel announces 16 more bytes to its TMA staging
+ *                          barrier than the copy delivers, so the staging wait
+ *                          gives up after about a second; the kernel records
+ *                          the failure in the device error word and leaves,
+ *                          the step's finish pass retires every active request
+ *                          with PMA_ERR_TIMEOUT (later sweeps skip their work)
+ *                          and pma_run returns PMA_ERR_TIMEOUT; the context
+ *                          stays usable.  0 = off (default). */
 enum { PMA_OPT_WINDOW_STEPS = 1, PMA_OPT_USE_GRAPHS = 2, PMA_OPT_LAUNCH_MODE = 3,
        PMA_OPT_TILE_2D = 4, PMA_OPT_TILE_3D = 5, PMA_OPT_MAX_ACTIVE = 6,
-       PMA_OPT_RESIDENT = 7, PMA_OPT_TIME_SWEEPS = 8, PMA_OPT_RESIDENT_STEPS = 9 };
+       PMA_OPT_RESIDENT = 7, PMA_OPT_TIME_SWEEPS = 8, PMA_OPT_RESIDENT_STEPS = 9,
+       PMA_OPT_TEST_STALL = 10 };
 enum { PMA_LAUNCH_BATCHED = 0, PMA_LAUNCH_PER_SUBDOMAIN = 1 };
 pma_status pma_set_option(pma_ctx *ctx, int32_t option, int64_t value);
 pma_status pma_get_option(pma_ctx *ctx, int32_t option, int64_t *value);

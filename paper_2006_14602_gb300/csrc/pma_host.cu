@@ -358,6 +358,7 @@ struct pma_ctx {
   // launches of every k-th step of a window (external event records inside
   // the window's graph)
   int opt_time_sweeps = 0;
+  int opt_test_stall = 0;  // test hook of the bounded TMA wait
   bool time_this_step = false;
   std::vector<cudaEvent_t> tev;
   int tev_used = 0;
@@ -944,6 +945,7 @@ LaunchArgs args_for(pma_ctx* c, int k, int t0, int n) {
   a.nb = c->d_nb;
   a.tmap = c->d_tmap;
   a.err = c->d_queue + 2 * NUM_CLS;
+  a.stall_bytes = c->opt_test_stall ? 16 : 0;
   a.probs = c->d_probs;
   a.st = c->d_state;
   a.part = c->d_part[k];
@@ -979,7 +981,7 @@ pma_status launch_step(pma_ctx* c) {
     st = time_mark(c);
     if (st != PMA_OK) return st;
     PMA_CK(launch_finish(c->d_fin[k], c->nfin[k], c->d_subs, c->d_probs, c->d_state,
-                         c->d_part[k], c->stream));
+                         c->d_part[k], c->d_queue + 2 * NUM_CLS, c->stream));
   }
   return PMA_OK;
 }
@@ -1087,6 +1089,10 @@ pma_status run_window(pma_ctx* c, int steps) {
                          cudaMemcpyDeviceToHost, c->stream));
   PMA_CK(cudaStreamSynchronize(c->stream));
   if (c->h_err != 0) {
+    // clear the word so that the context can run again
+    c->h_err = 0;
+    PMA_CK(cudaMemsetAsync(c->d_queue + 2 * NUM_CLS, 0, sizeof(unsigned int), c->stream));
+    PMA_CK(cudaStreamSynchronize(c->stream));
     set_err("a sweep kernel gave up waiting for its staging copies (bounded wait)");
     return PMA_ERR_TIMEOUT;
   }
@@ -1414,6 +1420,10 @@ pma_status pma_set_option(pma_ctx* c, int32_t opt, int64_t v) {
       if (v < 0) return PMA_ERR_INVALID;
       c->opt_resident = (int)std::min<int64_t>(v, kResClasses);
       break;
+    case PMA_OPT_TEST_STALL:
+      if (v < 0 || v > 1) return PMA_ERR_INVALID;
+      c->opt_test_stall = (int)v;
+      break;
     default: return PMA_ERR_INVALID;
   }
   c->graph_valid = false;
@@ -1433,6 +1443,7 @@ pma_status pma_get_option(pma_ctx* c, int32_t opt, int64_t* v) {
     case PMA_OPT_RESIDENT: *v = c->opt_resident; break;
     case PMA_OPT_TIME_SWEEPS: *v = c->opt_time_sweeps; break;
     case PMA_OPT_RESIDENT_STEPS: *v = c->opt_res_steps; break;
+    case PMA_OPT_TEST_STALL: *v = c->opt_test_stall; break;
     default: return PMA_ERR_INVALID;
   }
   return PMA_OK;
@@ -1957,6 +1968,7 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   la.nb = (const NbEnt*)(B + o_nb);
   la.tmap = nullptr;
   la.err = (unsigned int*)(B + o_q) + 2 * NUM_CLS;
+  la.stall_bytes = 0;
   la.probs = (const ProbDesc*)(B + o_prob);
   la.st = (ProbState*)(B + o_st);
   la.part = (Partial*)(B + o_part);
@@ -1969,7 +1981,8 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   for (;;) {
     for (int k = 0; k < window; ++k) {
       PMA_CK(launch_sweep(cls, 0, la, s));
-      PMA_CK(launch_finish((const int*)(B + o_fin), 1, la.subs, la.probs, la.st, la.part, s));
+      PMA_CK(launch_finish((const int*)(B + o_fin), 1, la.subs, la.probs, la.st, la.part, la.err,
+                           s));
     }
     PMA_CK(cudaMemcpyAsync(&ps, B + o_st, sizeof(ps), cudaMemcpyDeviceToHost, s));
     PMA_CK(cudaStreamSynchronize(s));

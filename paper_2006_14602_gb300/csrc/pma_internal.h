@@ -241,6 +241,7 @@ struct LaunchArgs {
   const NbEnt* nb;       // neighbour entries (3^dim per subdomain)
   const void* tmap;      // 2D: two tensor maps (128 B each) per subdomain, by parity
   unsigned int* err;     // device error word (bit 0: a bounded wait gave up)
+  int stall_bytes;       // test hook: extra bytes announced to the TMA barrier
   const ProbDesc* probs;
   ProbState* st;
   Partial* part;
@@ -263,7 +264,8 @@ cudaError_t prepare_sweep_kernels();
 // After a sweep launch: fold the tile records of the listed problem slots
 // (one warp each) and advance their scalars.
 cudaError_t launch_finish(const int* list, int n, const SubDesc* subs, const ProbDesc* probs,
-                          ProbState* st, const Partial* part, cudaStream_t s);
+                          ProbState* st, const Partial* part, const unsigned int* err,
+                          cudaStream_t s);
 
 // One combination job: a request's global mesh.  Jobs are laid out on a
 // flat grid of blocks of kCombineNodes nodes; block_begin is the job's first

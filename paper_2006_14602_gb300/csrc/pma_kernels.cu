@@ -234,14 +234,24 @@ __device__ __forceinline__ void advance_run(ProbState* ps, double theta, double 
 
 __global__ void k_finish(const int* __restrict__ list, int n, const SubDesc* __restrict__ subs,
                          const ProbDesc* __restrict__ probs, ProbState* st,
-                         const Partial* __restrict__ part) {
+                         const Partial* __restrict__ part, const unsigned int* err) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= n) return;
+  const unsigned int e0 = *(const volatile unsigned int*)err;
   const int p = list[w];
   ProbState* ps = st + p;
   const int phase = ps->phase;
   if (phase == PH_DONE) return;
+  if (e0 != 0) {
+    // a sweep gave up a bounded wait: the step's records are incomplete, so
+    // the problem retires with a timeout (later sweeps skip its work)
+    if (lane == 0) {
+      ps->status = PMA_ERR_TIMEOUT;
+      ps->phase = PH_DONE;
+    }
+    return;
+  }
   const ProbDesc& pd = probs[p];
   const int tb = pd.tile_begin, te = pd.tile_end;
   if (phase == PH_INIT_V) {
@@ -319,11 +329,12 @@ __global__ void k_finish(const int* __restrict__ list, int n, const SubDesc* __r
 }
 
 cudaError_t launch_finish(const int* list, int n, const SubDesc* subs, const ProbDesc* probs,
-                          ProbState* st, const Partial* part, cudaStream_t s) {
+                          ProbState* st, const Partial* part, const unsigned int* err,
+                          cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int threads = 128;
   const int blocks = (n * 32 + threads - 1) / threads;
-  k_finish<<<blocks, threads, 0, s>>>(list, n, subs, probs, st, part);
+  k_finish<<<blocks, threads, 0, s>>>(list, n, subs, probs, st, part, err);
   return cudaGetLastError();
 }
 
@@ -901,7 +912,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
       if (tr > 0) {
         if (tid == 0) {
           fence_proxy_async();
-          mbar_expect_tx(&tbar, (unsigned int)(SWp * tr * (int)sizeof(T)));
+          mbar_expect_tx(&tbar, (unsigned int)(SWp * tr * (int)sizeof(T) + a.stall_bytes));
           tma_load_2d(sv, (const char*)a.tmap + 128 * (2 * (size_t)H.w.sub + H.ps.parity),
                       i0 - 4, j0 - 1, &tbar);
         }

@@ -47,6 +47,7 @@ PMA_OPT_MAX_ACTIVE = 6
 PMA_OPT_RESIDENT = 7
 PMA_OPT_TIME_SWEEPS = 8
 PMA_OPT_RESIDENT_STEPS = 9
+PMA_OPT_TEST_STALL = 10
 PMA_LAUNCH_BATCHED = 0
 PMA_LAUNCH_PER_SUBDOMAIN = 1
 
@@ -393,7 +394,7 @@ class Context:
              "launch_mode": PMA_OPT_LAUNCH_MODE, "tile_2d": PMA_OPT_TILE_2D,
              "tile_3d": PMA_OPT_TILE_3D, "max_active": PMA_OPT_MAX_ACTIVE,
              "resident": PMA_OPT_RESIDENT, "time_sweeps": PMA_OPT_TIME_SWEEPS,
-             "resident_steps": PMA_OPT_RESIDENT_STEPS}
+             "resident_steps": PMA_OPT_RESIDENT_STEPS, "test_stall": PMA_OPT_TEST_STALL}
 
     def set(self, name: str, value: int):
         st = pma_set_option(self.h, self._OPTS[name], int(value))
