@@ -286,6 +286,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, i
       "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// 3D tiled copy of the box at (x, y, z) (x as for the 2D copy).
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
 // Wait until the barrier's phase with parity `phase` has completed, for at
 // most about a second of SM clock; false if it gave up.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int phase) {

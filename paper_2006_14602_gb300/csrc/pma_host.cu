@@ -592,7 +592,7 @@ void push_items(const HostSub& hs, int dim, bool fp64, int tile_id, int sidx, in
       for (int y = 0; y < hs.n[1]; y += rows) {
         const int rr = std::min(rows, hs.n[1] - y);
         wl.push_back(WorkItem{sidx, slot, x | (y << 16), cols | (rr << 16), 0,
-                              band_flags(hs, x, y, cols, rr), tr, 0});
+                              band_flags(hs, x, y, cols, rr), tr, -1});
       }
     }
   } else {
@@ -605,12 +605,15 @@ void push_items(const HostSub& hs, int dim, bool fp64, int tile_id, int sidx, in
       while (rows > 1 && ((rows + 2) * swp * (t3.tz + 2) + 5 * cr > t3.smax ||
                           (rows + 2) * (t3.tz + 2) > 8 * t3.threads))
         --rows;
+      // one TMA box per item where the subdomain is one strip and the box
+      // fits the copy engine's 256 x 256 x 256 limit
+      const int t3ok = (cols == hs.n[0] && swp <= 256 && rows + 2 <= 256 && t3.tz + 2 <= 256);
       for (int y = 0; y < hs.n[1]; y += rows) {
         const int rr = std::min(rows, hs.n[1] - y);
         for (int z = 0; z < hs.n[2]; z += t3.tz) {
           const int d = std::min(t3.tz, hs.n[2] - z);
           wl.push_back(WorkItem{sidx, slot, x | (y << 16), cols | (rr << 16), z | (d << 16), 0,
-                                0, 0});
+                                t3ok, -1});
         }
       }
     }
@@ -637,25 +640,78 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// Tensor maps of a 2D subdomain's two state buffers for the TMA staging of
-// its bands: the buffer as a (pitch x n1) array of rows, boxes of
-// (SWp x box_rows) elements, zero fill outside.  Returns false (the bands
-// then stage with cp.async) if the encoder is missing or refuses.
-bool encode_band_maps(const SubDesc& sd, int esize, int cols, int box_rows, CUtensorMap out[2]) {
+// Tensor maps of a subdomain's two state buffers for the TMA staging of its
+// work items: the buffer as a (pitch x n1 [x n2]) array, boxes of
+// (SWp x box_rows [x box_planes]) elements, zero fill outside.  Returns
+// false (the items then stage with cp.async) if the encoder is missing or
+// refuses.
+bool encode_box_maps(const SubDesc& sd, int dim, int esize, int cols, int box_rows,
+                     int box_planes, CUtensorMap out[2]) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)sd.pitch, (cuuint64_t)sd.n[1]};
-  const cuuint64_t strides[1] = {(cuuint64_t)sd.pitch * (cuuint64_t)esize};
-  const cuuint32_t box[2] = {(cuuint32_t)(((cols + 3) & ~3) + 8), (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
+  const cuuint64_t dims[3] = {(cuuint64_t)sd.pitch, (cuuint64_t)sd.n[1], (cuuint64_t)sd.n[2]};
+  const cuuint64_t strides[2] = {(cuuint64_t)sd.pitch * (cuuint64_t)esize,
+                                 (cuuint64_t)sd.pitch * (cuuint64_t)sd.n[1] * (cuuint64_t)esize};
+  const cuuint32_t box[3] = {(cuuint32_t)(((cols + 3) & ~3) + 8), (cuuint32_t)box_rows,
+                             (cuuint32_t)box_planes};
+  const cuuint32_t estr[3] = {1, 1, 1};
   for (int p = 0; p < 2; ++p) {
     if (fn(&out[p], esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-           2, sd.v[p], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           (cuuint32_t)dim, sd.v[p], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
   }
   return true;
+}
+
+// Tensor maps for the TMA items of one subdomain (items wl[b, e)): 2D, one
+// pair for the subdomain's band box; 3D, one pair per distinct box extent
+// (full / last rows x full / last planes).  Items whose maps cannot be
+// encoded fall back to cp.async.
+void assign_maps(const SubDesc& sd, int dim, int esize, int n0, WorkItem* w, int n,
+                 std::vector<CUtensorMap>& maps) {
+  if (n <= 0 || w[0].tma_rows <= 0) return;
+  if (dim == 2) {
+    const size_t base = maps.size();
+    maps.resize(base + 2);
+    if (encode_box_maps(sd, 2, esize, n0, w[0].tma_rows, 1, &maps[base])) {
+      for (int t = 0; t < n; ++t) w[t].tma_map = (int)base;
+    } else {
+      maps.resize(base);
+      for (int t = 0; t < n; ++t) w[t].tma_rows = 0;
+    }
+    return;
+  }
+  int ext[4][3], nm = 0;  // (rows, planes, map index)
+  for (int t = 0; t < n; ++t) {
+    const int rr = w[t].ext >> 16, d = w[t].kz >> 16;
+    int m = -1;
+    bool seen = false;
+    for (int q = 0; q < nm; ++q)
+      if (ext[q][0] == rr && ext[q][1] == d) {
+        m = ext[q][2];
+        seen = true;
+      }
+    if (!seen && nm < 4) {
+      const size_t base = maps.size();
+      maps.resize(base + 2);
+      if (encode_box_maps(sd, 3, esize, n0, rr + 2, d + 2, &maps[base])) {
+        m = (int)base;
+      } else {
+        maps.resize(base);
+      }
+      ext[nm][0] = rr;
+      ext[nm][1] = d;
+      ext[nm][2] = m;
+      ++nm;
+    }
+    if (m < 0) {
+      w[t].tma_rows = 0;
+    } else {
+      w[t].tma_map = m;
+    }
+  }
 }
 
 // Neighbour entries of the subdomains subs[0..n) of one problem (blocks in
@@ -731,11 +787,8 @@ pma_status rebuild(pma_ctx* c) {
       if (live)
         push_items(hs, r.dim, r.esize == 8, c->tile_id[r.cls], (int)c->h_subs.size(), r.slot, wl);
       sd.tile_end = (int)wl.size();
-      c->h_tmap.resize(2 * (c->h_subs.size() + 1));
-      if (sd.tile_end > sd.tile_begin && wl[sd.tile_begin].tma_rows > 0 &&
-          !encode_band_maps(sd, r.esize, hs.n[0], wl[sd.tile_begin].tma_rows,
-                            &c->h_tmap[2 * c->h_subs.size()]))
-        for (int t = sd.tile_begin; t < sd.tile_end; ++t) wl[t].tma_rows = 0;
+      assign_maps(sd, r.dim, r.esize, hs.n[0], wl.data() + sd.tile_begin,
+                  sd.tile_end - sd.tile_begin, c->h_tmap);
       c->h_subs.push_back(sd);
     }
     pd.tile_end = (int)wl.size();

@@ -140,10 +140,12 @@ struct alignas(16) WorkItem {
   // row (each row flagged once); bit 4 / 5 = staged column 4 / cols + 3
   // (local column 0 / n0 - 1) is a transmission column.  3D: 0.
   int flags;
-  // 2D: rows of the band's TMA box (the subdomain's full bands plus the
-  // halo rows; the box is SWp columns wide), 0 = staged by cp.async
+  // TMA staging: 2D: rows of the band's box (the subdomain's full bands
+  // plus the halo rows; the box is SWp columns wide); 3D: 1 (the box is the
+  // item's staged box); 0 = staged by cp.async.  tma_map: index of the
+  // item's tensor map for buffer 0 (buffer 1: the next one).
   int tma_rows;
-  int pad;
+  int tma_map;
 };
 
 struct Partial {
@@ -239,7 +241,7 @@ struct LaunchArgs {
   int nwork;             // work items of this launch
   const SubDesc* subs;
   const NbEnt* nb;       // neighbour entries (3^dim per subdomain)
-  const void* tmap;      // 2D: two tensor maps (128 B each) per subdomain, by parity
+  const void* tmap;      // tensor maps (128 B each), see WorkItem::tma_map
   unsigned int* err;     // device error word (bit 0: a bounded wait gave up)
   int stall_bytes;       // test hook: extra bytes announced to the TMA barrier
   const ProbDesc* probs;

@@ -913,7 +913,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
         if (tid == 0) {
           fence_proxy_async();
           mbar_expect_tx(&tbar, (unsigned int)(SWp * tr * (int)sizeof(T) + a.stall_bytes));
-          tma_load_2d(sv, (const char*)a.tmap + 128 * (2 * (size_t)H.w.sub + H.ps.parity),
+          tma_load_2d(sv, (const char*)a.tmap + 128 * ((size_t)H.w.tma_map + H.ps.parity),
                       i0 - 4, j0 - 1, &tbar);
         }
       } else {
@@ -1573,9 +1573,10 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int NW = NT / 32;
   constexpr int HMAX = 8;  // halo rows per thread (host: (rows+2)(TZ+2) <= 8 NT)
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
   T* sv = (T*)dyn_smem;     // staged box + column tables (dynamic size)
   __shared__ __align__(16) SmemHdr<T> HB[2];
+  __shared__ __align__(8) unsigned long long tbar;  // TMA staging barrier
   __shared__ int s_t[2];
   __shared__ T red_t[4 * NW];
   __shared__ T red_f[3 * NW];
@@ -1584,6 +1585,9 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
   const int tend = a.t0 + a.nwork;
   int t_next = 0;
   WorkItem w_next;
+  unsigned int tph = 0;  // parity of the TMA barrier's next phase
+  if (tid == 0) mbar_init(&tbar, 1);
+  __syncthreads();
   if (tid == 0) {
     const int t0 = pull_item(a);
     s_t[0] = t0;
@@ -1662,15 +1666,27 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
       const bool plx = faces & 1, phx = faces & 2, ply = faces & 4, phy = faces & 8;
       const bool plz = faces & 16, phz = faces & 32;
       const T corr = (T)H.ps.corr;
-      // (a) 16-byte asynchronous copies of every staged row
-      for (int e = tid; e < nrow * cpr; e += NT) {
-        const int rr = qdiv(e, cpr, inv_cpr), k = e - rr * cpr;
-        const int gs = i0 - 4 + k * VW;
-        if (gs >= 0 && gs + VW <= pitch) {
-          const int lz = qdiv(rr, SHY, inv_shy), ly = rr - lz * SHY;
-          const int jj = reflect_clamp(j0 - 1 + ly, n1, ply, phy);
-          const int kk = reflect_clamp(k0 - 1 + lz, n2, plz, phz);
-          cp_async16(sv + lz * PS + ly * SWp + k * VW, src + kk * ppitch + jj * pitch + gs);
+      // (a) the staged box: one TMA copy where the subdomain has tensor maps
+      //     (zeros outside the buffer, mirror rows and planes fixed below),
+      //     else 16-byte asynchronous copies of every staged row
+      const bool tma = a.tmap != nullptr && H.w.tma_rows > 0;
+      if (tma) {
+        if (tid == 0) {
+          fence_proxy_async();
+          mbar_expect_tx(&tbar, (unsigned int)(PS * SHZ * (int)sizeof(T) + a.stall_bytes));
+          tma_load_3d(sv, (const char*)a.tmap + 128 * ((size_t)H.w.tma_map + H.ps.parity),
+                      i0 - 4, j0 - 1, k0 - 1, &tbar);
+        }
+      } else {
+        for (int e = tid; e < nrow * cpr; e += NT) {
+          const int rr = qdiv(e, cpr, inv_cpr), k = e - rr * cpr;
+          const int gs = i0 - 4 + k * VW;
+          if (gs >= 0 && gs + VW <= pitch) {
+            const int lz = qdiv(rr, SHY, inv_shy), ly = rr - lz * SHY;
+            const int jj = reflect_clamp(j0 - 1 + ly, n1, ply, phy);
+            const int kk = reflect_clamp(k0 - 1 + lz, n2, plz, phz);
+            cp_async16(sv + lz * PS + ly * SWp + k * VW, src + kk * ppitch + jj * pitch + gs);
+          }
         }
       }
       cp_async_commit();
@@ -1737,7 +1753,43 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
         }
       }
       cp_async_wait_all();
-      __syncthreads();
+      bool gave_up = false;
+      if (tma) {
+        gave_up = !mbar_wait(&tbar, tph);
+        tph ^= 1;
+      }
+      if (__syncthreads_or(gave_up)) {
+        // the box never arrived: report, give the copy one more bounded
+        // wait, and leave (the host turns the error word into a status)
+        if (tid == 0) {
+          atomicOr(a.err, 1u);
+          mbar_wait(&tbar, tph ^ 1);
+        }
+        break;
+      }
+      if (tma && ((ply && j0 == 0) || (phy && j0 + rows == n1))) {
+        // Neumann mirror rows of a TMA box in every staged plane: row 0 <-
+        // row 2, row rows+1 <- row rows-1 (x-halo columns: written by (c))
+        for (int e = tid; e < SHZ * SWp; e += NT) {
+          const int lz = e / SWp, c = e - lz * SWp;
+          if ((left && c == 3) || (right && c == cols + 4)) continue;
+          T* const pl = sv + lz * PS;
+          if (ply && j0 == 0) pl[c] = pl[2 * SWp + c];
+          if (phy && j0 + rows == n1) pl[(rows + 1) * SWp + c] = pl[(rows - 1) * SWp + c];
+        }
+        __syncthreads();
+      }
+      if (tma && ((plz && k0 == 0) || (phz && k0 + depth == n2))) {
+        // then the mirror planes: plane 0 <- plane 2, plane depth+1 <-
+        // plane depth-1 (so that edges and corners mirror in both axes)
+        for (int e = tid; e < PS; e += NT) {
+          const int c = e % SWp;
+          if ((left && c == 3) || (right && c == cols + 4)) continue;
+          if (plz && k0 == 0) sv[e] = sv[2 * PS + e];
+          if (phz && k0 + depth == n2) sv[(depth + 1) * PS + e] = sv[(depth - 1) * PS + e];
+        }
+        __syncthreads();
+      }
       // (c) halos, then the transmission offset on the box perimeter:
       //     transmission planes (whole), rows in other planes (whole),
       //     columns 0 / n0-1 elsewhere; halo columns were written by (b)
