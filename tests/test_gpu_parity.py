@@ -83,6 +83,19 @@ def test_subdomains_wider_than_one_band(prec):
     _check(prob, psi=False)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,parts,o", [((123, 201), (1, 1), 0), ((150, 400), (2, 2), 6)])
+def test_tma_staged_bands_ragged(prec, n, parts, o):
+    """Subdomains of several bands staged by TMA boxes: the last band of a
+    subdomain is shorter than its box (rows beyond it or outside the buffer
+    are fetched and ignored), mirror rows come from inside the box on
+    physical faces, transmission rows and columns on inner ones."""
+    prob = W.Problem(dim=2, n=(n[0], n[1], 1), monitor=W.ring_monitor(), parts=(parts[0], parts[1], 1),
+                     overlap=o, dt=W.dt_for((n[0], n[1], 1), 2), tol=0.0, max_steps=40,
+                     precision=prec)
+    _check(prob, psi=False)
+
+
 @pytest.mark.parametrize("mon", ["sine", "bumps", "product", "burgers"])
 def test_monitor_kinds_2d(mon):
     rng = np.random.default_rng(5)
@@ -157,6 +170,17 @@ def test_dd_3d(prec, n, parts, o):
     prob = W.Problem(dim=3, n=n, monitor=W.shell_monitor(), parts=parts, overlap=o,
                      dt=W.dt_for(n, 3, cfl=0.05), tol=0.0, max_steps=60, precision=prec)
     _check(prob)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tma_staged_boxes_all_extents(prec):
+    """3D boxes of four extents in one subdomain (full / last rows x full /
+    last planes, one pair of tensor maps each), mirror rows and planes on
+    the physical faces."""
+    n = (30, 44, 27)
+    prob = W.Problem(dim=3, n=n, monitor=W.shell_monitor(), parts=(1, 2, 2), overlap=4,
+                     dt=W.dt_for(n, 3, cfl=0.05), tol=0.0, max_steps=30, precision=prec)
+    _check(prob, psi=False)
 
 
 @pytest.mark.parametrize("mon", ["tanh_sphere", "nine_spheres"])
