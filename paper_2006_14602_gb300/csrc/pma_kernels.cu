@@ -235,6 +235,10 @@ __device__ __forceinline__ void advance_run(ProbState* ps, double theta, double 
 __global__ void k_finish(const int* __restrict__ list, int n, const SubDesc* __restrict__ subs,
                          const ProbDesc* __restrict__ probs, ProbState* st,
                          const Partial* __restrict__ part, const unsigned int* err) {
+  // the next sweep may be launched at once (its CTAs wait for this grid);
+  // this grid waits for the sweep before it reads the records
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= n) return;
@@ -334,7 +338,16 @@ cudaError_t launch_finish(const int* list, int n, const SubDesc* subs, const Pro
   if (n <= 0) return cudaSuccess;
   const int threads = 128;
   const int blocks = (n * 32 + threads - 1) / threads;
-  k_finish<<<blocks, threads, 0, s>>>(list, n, subs, probs, st, part, err);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_finish, list, n, subs, probs, st, part, err);
   return cudaGetLastError();
 }
 
@@ -814,6 +827,9 @@ __device__ __forceinline__ void issue_hdr(const LaunchArgs& a, BandHdr<T>& H, co
 // (a multiple of 4) wide.
 template <typename T, int NT, int SMAX>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2d(LaunchArgs a) {
+  // programmatic dependent launch: wait until the preceding kernel of the
+  // stream has completed and its writes are visible
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int NW = NT / 32;
   __shared__ __align__(128) T sv[SMAX];
@@ -1178,6 +1194,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
     }
   }
   if (tid == 0) queue_exit(a);
+  // this CTA has run out of work: the next kernel of the stream (launched
+  // as a programmatic dependent) may be scheduled while the last CTAs finish
+  asm volatile("griddepcontrol.launch_dependents;");
 }
 
 // ---------------------------------------------------------------- resident 2D
@@ -1570,6 +1589,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_res2
 // values of the 19-point stencils of its 4 nodes with aligned vector loads.
 template <typename T, int NT, int TZ, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
+  // programmatic dependent launch: wait until the preceding kernel of the
+  // stream has completed and its writes are visible
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int NW = NT / 32;
   constexpr int HMAX = 8;  // halo rows per thread (host: (rows+2)(TZ+2) <= 8 NT)
@@ -2065,6 +2087,9 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
     }
   }
   if (tid == 0) queue_exit(a);
+  // this CTA has run out of work: the next kernel of the stream (launched
+  // as a programmatic dependent) may be scheduled while the last CTAs finish
+  asm volatile("griddepcontrol.launch_dependents;");
 }
 
 // ---------------------------------------------------------------- dispatch
@@ -2170,7 +2195,17 @@ cudaError_t launch_sweep(int cls, int tile_id, const LaunchArgs& a, cudaStream_t
   if (!fn) return cudaErrorInvalidValue;
   if (a.nwork <= 0 || a.grid <= 0) return cudaSuccess;
   void* args[] = {(void*)&a};
-  return cudaLaunchKernel(fn, dim3(a.grid), dim3(nt), args, (size_t)dyn, s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.grid);
+  cfg.blockDim = dim3(nt);
+  cfg.dynamicSmemBytes = (size_t)dyn;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 cudaError_t prepare_sweep_kernels() {
