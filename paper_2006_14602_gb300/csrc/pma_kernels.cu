@@ -2098,7 +2098,7 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
 // tables fit in nodes x factor / 10 elements (bands get fewer rows, or
 // narrower strips, where the halo would not fit).
 #define PMA_T2D(X) X(128, 3072, 1536, 16) X(128, 2048, 1024, 30) X(128, 4096, 2048, 14) \
-                   X(128, 5120, 2560, 14)
+                   X(128, 5120, 2560, 14) X(128, 768, 384, 30)
 #define PMA_SMAX(n, f) (((n) * (f) / 10) & ~3)
 // 3D: (threads, nodes per plane box, planes FP32, planes FP64, dynamic
 // shared memory in KiB for the staged box and the column tables, FP32 CTAs
