@@ -396,6 +396,14 @@ const char *pma_status_str(int32_t status);
 /* Last CUDA / validation error text of this thread (never NULL). */
 const char *pma_last_error(void);
 int32_t pma_abi_version(void);
+/* Host-only consistency checks of the library's device tables (neighbour
+ * entries of the transmission gathers against the owner of each node by
+ * the decomposition's core boundaries, transmission-row/column flags of the
+ * staged 2D bands, exact tiling and shared-memory / TMA limits of the work
+ * items of every compiled shape) on built-in decompositions.  Touches no
+ * device.  Returns the number of failed checks (0 = pass); the first
+ * failure is described by pma_last_error.                                */
+int32_t pma_selftest_tables(void);
 
 #ifdef __cplusplus
 }

@@ -2061,3 +2061,181 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   }
   return (pma_status)ps.status;
 }
+
+// ============================================================== self-test
+// Host-only consistency checks of the tables the sweep kernels index (no
+// device is touched; buffer addresses are offsets into a dummy block):
+//   * the neighbour table: for sampled local nodes of every subdomain, the
+//     entry the kernels select (block offset by core ranges, 3^dim entries
+//     per subdomain) addresses the same element as the owner found directly
+//     from the core boundaries of the decomposition (Eq.
+//     transmission_condition3 with the owner-takes reading of the overlap);
+//   * the transmission-row and -column flags of every staged 2D band
+//     against a direct classification of its staged rows and columns;
+//   * the work items of every compiled shape: an exact tiling of each
+//     subdomain, the shared-memory budget, and the TMA box limits.
+// Returns the number of failed checks; the first failure is described by
+// pma_last_error.
+extern "C" int32_t pma_selftest_tables(void) {
+  struct Case {
+    int dim, n[3], parts[3], o;
+  };
+  const Case cases[] = {{2, {45, 37, 1}, {3, 2, 1}, 5},    {2, {97, 65, 1}, {4, 3, 1}, 8},
+                        {2, {150, 400, 1}, {2, 2, 1}, 6},  {2, {513, 17, 1}, {16, 1, 1}, 4},
+                        {2, {2300, 40, 1}, {2, 1, 1}, 6},  {3, {19, 17, 15}, {2, 2, 2}, 4},
+                        {3, {30, 44, 27}, {1, 2, 2}, 4},   {3, {40, 9, 11}, {3, 1, 1}, 3}};
+  int bad = 0;
+  std::string first;
+  auto fail = [&](const std::string& what) {
+    if (bad++ == 0) first = what;
+  };
+  for (const Case& cs : cases) {
+    for (int esize : {4, 8}) {
+      Request r;
+      r.g.dim = cs.dim;
+      for (int a = 0; a < 3; ++a) {
+        r.g.n[a] = cs.n[a];
+        r.g.lo[a] = 0.0;
+        r.g.hi[a] = 1.0;
+        r.d.parts[a] = cs.parts[a];
+      }
+      r.d.overlap = cs.o;
+      r.d.transmission = PMA_TRANSMISSION_PARALLEL;
+      r.m.kind = PMA_MON_SUM;
+      r.m.nterms = 0;
+      r.m.base = 1.0;
+      r.p.dt = 1e-4;
+      r.p.tol = 0.0;
+      r.p.max_steps = 1;
+      r.p.check_every = 1;
+      r.p.precision = esize == 8 ? PMA_FP64 : PMA_FP32;
+      if (build_request(r) != PMA_OK) {
+        fail("build_request refused a self-test case");
+        continue;
+      }
+      // buffer addresses inside a host block: compared, never dereferenced
+      std::vector<char> host_block(r.bytes + 64);
+      char* const block = host_block.data();
+      std::vector<SubDesc> subs;
+      for (const HostSub& hs : r.subs) {
+        SubDesc sd{};
+        for (int a = 0; a < 3; ++a) {
+          sd.n[a] = hs.n[a];
+          sd.g0[a] = hs.g0[a];
+          sd.clo[a] = hs.clo[a];
+          sd.chi[a] = hs.chi[a];
+          sd.k[a] = hs.k[a];
+        }
+        sd.faces = hs.faces;
+        sd.idx = hs.idx;
+        sd.pitch = hs.pitch;
+        sd.v[0] = block + hs.off[0];
+        sd.v[1] = block + hs.off[1];
+        subs.push_back(sd);
+      }
+      // neighbour table against the owner from the core boundaries
+      std::vector<NbEnt> nb;
+      fill_nb(subs.data(), (int)subs.size(), r.dim, r.parts, esize, nb);
+      const int per = r.dim == 3 ? 27 : 9;
+      if ((int)nb.size() != per * (int)subs.size()) fail("neighbour table size");
+      for (size_t s = 0; s < subs.size() && nb.size() == per * subs.size(); ++s) {
+        const SubDesc& me = subs[s];
+        int samp[3][4], ns[3];
+        for (int a = 0; a < 3; ++a) {
+          const int n = me.n[a];
+          ns[a] = 0;
+          for (int v : {0, 1, n / 2, n - 1})
+            if (v >= 0 && v < n) samp[a][ns[a]++] = v;
+        }
+        for (int ia = 0; ia < ns[0]; ++ia)
+          for (int ja = 0; ja < ns[1]; ++ja)
+            for (int la = 0; la < ns[2]; ++la) {
+              const int loc[3] = {samp[0][ia], samp[1][ja], samp[2][la]};
+              int kk[3], q[3];
+              for (int a = 0; a < 3; ++a) {
+                const int g = me.g0[a] + loc[a];
+                kk[a] = 0;
+                while (kk[a] + 1 < r.parts[a] && g >= r.bcore[a][kk[a] + 1]) ++kk[a];
+                q[a] = loc[a] < me.clo[a] ? 0 : (loc[a] > me.chi[a] ? 2 : 1);
+              }
+              const SubDesc& o = subs[(kk[2] * r.parts[1] + kk[1]) * r.parts[0] + kk[0]];
+              const NbEnt& e = nb[s * per + q[0] + 3 * q[1] + (per == 27 ? 9 * q[2] : 0)];
+              for (int p = 0; p < 2; ++p) {
+                const long long want =
+                    (long long)((const char*)o.v[p] - block) / esize + (me.g0[0] + loc[0] - o.g0[0]) +
+                    (long long)o.pitch * ((me.g0[1] + loc[1] - o.g0[1]) +
+                                          (long long)o.n[1] * (me.g0[2] + loc[2] - o.g0[2]));
+                const long long got = e.v[p] == nullptr
+                                          ? -1
+                                          : (long long)((const char*)e.v[p] - block) / esize +
+                                                loc[0] + (long long)e.pitch * loc[1] +
+                                                (long long)e.plane * loc[2];
+                if (want != got) fail("neighbour entry addresses the wrong owner element");
+              }
+            }
+      }
+      // work items of every compiled shape
+      const int nshape = r.dim == 2 ? tile2d_count() : tile3d_count();
+      for (int id = 0; id < nshape; ++id) {
+        for (size_t si = 0; si < r.subs.size(); ++si) {
+          const HostSub& hs = r.subs[si];
+          std::vector<WorkItem> wl;
+          push_items(hs, r.dim, esize == 8, id, (int)si, 0, wl);
+          std::vector<unsigned char> cover((size_t)hs.n[0] * hs.n[1] * hs.n[2], 0);
+          for (const WorkItem& w : wl) {
+            const int i0 = w.ij & 0xffff, j0 = w.ij >> 16;
+            const int cols = w.ext & 0xffff, rows = w.ext >> 16;
+            const int k0 = r.dim == 3 ? (w.kz & 0xffff) : 0, dep = r.dim == 3 ? (w.kz >> 16) : 1;
+            const int cr = (cols + 3) & ~3, swp = cr + 8;
+            for (int l = k0; l < k0 + dep; ++l)
+              for (int j = j0; j < j0 + rows; ++j)
+                for (int i = i0; i < i0 + cols; ++i) {
+                  if (i >= hs.n[0] || j >= hs.n[1] || l >= hs.n[2]) {
+                    fail("work item beyond its subdomain");
+                    continue;
+                  }
+                  cover[((size_t)l * hs.n[1] + j) * hs.n[0] + i] += 1;
+                }
+            if (r.dim == 2) {
+              const Tile2D t2 = tile2d_shape(id, esize == 8);
+              const int box = w.tma_rows > 0 ? w.tma_rows : rows + 2;
+              if (box * swp + 5 * cr > t2.smax) fail("2D band exceeds its shared memory");
+              if (w.tma_rows > 0 && (cols != hs.n[0] || swp > 256 || w.tma_rows > 256 ||
+                                     w.tma_rows < rows + 2))
+                fail("2D TMA box outside the copy engine's limits");
+              // transmission flags against the staged rows and columns
+              const int n1 = hs.n[1], f = hs.faces;
+              const int dly = (f & 4) ? -1 : 0, dhy = (f & 8) ? -1 : n1 - 1;
+              const int sh = rows + 2;
+              const int cand[4] = {0, 1, sh - 2, sh - 1};
+              for (int rr = 0; rr < sh; ++rr) {
+                const int jj = reflect_host(j0 - 1 + rr, n1, f & 4, f & 8);
+                const bool trans = jj == dly || jj == dhy;
+                bool flagged = false;
+                for (int qq = 0; qq < 4; ++qq)
+                  if ((w.flags >> qq) & 1) flagged = flagged || cand[qq] == rr;
+                if (trans != flagged) fail("2D band transmission-row flags");
+              }
+              const bool cl = !(f & 1) && i0 == 0, ch = !(f & 2) && i0 + cols == hs.n[0];
+              if (((w.flags >> 4) & 1) != (cl ? 1 : 0) || ((w.flags >> 5) & 1) != (ch ? 1 : 0))
+                fail("2D band transmission-column flags");
+            } else {
+              const Tile3D t3 = tile3d_shape(id, esize == 8);
+              if ((rows + 2) * swp * (dep + 2) + 5 * cr > t3.smax)
+                fail("3D box exceeds its shared memory");
+              if (w.tma_rows > 0 && (cols != hs.n[0] || swp > 256 || rows + 2 > 256))
+                fail("3D TMA box outside the copy engine's limits");
+            }
+          }
+          for (unsigned char c : cover)
+            if (c != 1) {
+              fail("work items do not tile the subdomain exactly once");
+              break;
+            }
+        }
+      }
+    }
+  }
+  if (bad) set_err("pma_selftest_tables: " + std::to_string(bad) + " failed checks; first: " + first);
+  return bad;
+}

@@ -116,6 +116,7 @@ _SIGS = {
     "pma_status_str": (C.c_char_p, [C.c_int32]),
     "pma_last_error": (C.c_char_p, []),
     "pma_abi_version": (C.c_int32, []),
+    "pma_selftest_tables": (C.c_int32, []),
     "pma_create": (C.c_int, [_P(C.c_void_p), C.c_int, C.c_size_t, C.c_void_p]),
     "pma_destroy": (C.c_int, [C.c_void_p]),
     "pma_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
@@ -186,6 +187,12 @@ def pma_last_error() -> str:
 
 def pma_abi_version() -> int:
     return _call("pma_abi_version")
+
+
+def pma_selftest_tables() -> int:
+    """Host-only consistency checks of the device tables (no GPU used);
+    returns the number of failed checks."""
+    return _call("pma_selftest_tables")
 
 
 def pma_create(device: int = 0, mem_budget_bytes: int = 0, cuda_stream: int = 0):

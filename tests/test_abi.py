@@ -109,3 +109,12 @@ def test_problem_marshalling():
     assert p.precision == 0 and p.max_steps == 2000
     with pytest.raises(ValueError):
         pma.to_structs(W.small_case().replace(rhs="root"))
+
+
+def test_host_tables_selftest(lib):
+    """The library's host-only self-test of the tables its kernels index:
+    neighbour entries of the transmission gathers against the owners from
+    the decomposition's core boundaries, the staged bands' transmission
+    flags, and the work items' tiling and shared-memory / TMA limits."""
+    n = pma.pma_selftest_tables()
+    assert n == 0, pma.pma_last_error()
