@@ -230,9 +230,9 @@ pma_status pma_destroy(pma_ctx *ctx);
  *                          so resident requests can run several band windows'
  *                          worth of steps while the band work of a window
  *                          runs beside them (results do not depend on it).
- *   PMA_OPT_TEST_STALL     test hook of the bounded waits: 1 = the 2D band
- *                          kernel announces 16 more bytes to its TMA staging
- *                          barrier than the copy delivers, so the staging wait
+ *   PMA_OPT_TEST_STALL     test hook of the bounded waits: 1 = the 2D and 3D
+ *                          sweep kernels announce 16 more bytes to their TMA
+ *                          staging barrier than the copy delivers, so the wait
  *                          gives up after about a second; the kernel records
  *                          the failure in the device error word and leaves,
  *                          the step's finish pass retires every active request
