@@ -50,7 +50,7 @@ def _rate(probs, steps: int, windows: int, device: int, **options) -> float:
 
 
 def autotune(probs: Sequence, device: int = 0, windows: int = 3,
-             window_candidates: Sequence[int] = (32, 64, 128),
+             window_candidates: Sequence[int] = (32, 64, 128, 256),
              trial_steps: int = 32, **options) -> Dict:
     """Pick tile_2d, tile_3d and window_steps for the batch `probs`.
 
