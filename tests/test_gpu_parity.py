@@ -96,6 +96,20 @@ def test_tma_staged_bands_ragged(prec, n, parts, o):
     _check(prob, psi=False)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,n,parts,o", [(2, (3, 41, 1), (1, 2, 1), 2), (2, (41, 3, 1), (2, 1, 1), 2),
+                                           (2, (3, 3, 1), (1, 1, 1), 0), (3, (3, 3, 3), (1, 1, 1), 0),
+                                           (3, (5, 4, 3), (1, 1, 1), 0), (3, (3, 17, 9), (1, 2, 1), 2)])
+def test_degenerate_minimum_grids(prec, dim, n, parts, o):
+    """The smallest grids the method allows (3 nodes on an axis, the
+    thinnest decompositions): runs of 4 nodes padded past the grid, boxes of
+    a few columns, every node on a physical or transmission face."""
+    prob = W.Problem(dim=dim, n=n, monitor=W.ring_monitor(dim) if dim == 2 else W.shell_monitor(),
+                     parts=parts, overlap=o, dt=W.dt_for(n, dim, cfl=0.1 if dim == 2 else 0.05),
+                     tol=0.0, max_steps=20, precision=prec)
+    _check(prob, psi=False)
+
+
 @pytest.mark.parametrize("mon", ["sine", "bumps", "product", "burgers"])
 def test_monitor_kinds_2d(mon):
     rng = np.random.default_rng(5)
