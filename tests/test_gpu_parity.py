@@ -409,6 +409,24 @@ def test_config2_full_size(mon):
     _check(p64.replace(precision="fp32"), ref)
 
 
+def test_uneven_batch_full_size_sampled():
+    """The uneven batch at full size (512 requests, 4,648 subdomains) in one
+    context with the bench's launch configuration, capped at 30 steps; the
+    largest request and a seeded sample checked one by one against the
+    oracle (FP32 sweep against FP64)."""
+    probs = [p.replace(max_steps=30) for p in W.config4()]
+    res = pma.solve_many(probs, window_steps=128)
+    sizes = [p.n[0] * p.n[1] for p in probs]
+    rng = np.random.default_rng(14602)
+    picks = {int(np.argmax(sizes))} | {int(k) for k in rng.choice(len(probs), 5, replace=False)}
+    for k in sorted(picks):
+        ref = oracle.solve(probs[k].replace(precision="fp64"))
+        x, _, info = res[k]
+        assert info.steps == ref.steps, (k, info.steps, ref.steps)
+        assert pma.STATUS_NAMES[info.status] == ref.status
+        assert np.abs(x - ref.x).max() / _size(probs[k]) <= TOL32, k
+
+
 def test_config3_full_size_fp32_vs_oracle():
     """129^3 in 2x2x2 subdomains (overlap 6), FP32 sweep vs the FP64 oracle."""
     prob = W.config3("fp32", max_steps=25)
