@@ -427,6 +427,20 @@ def test_uneven_batch_full_size_sampled():
         assert np.abs(x - ref.x).max() / _size(probs[k]) <= TOL32, k
 
 
+@pytest.mark.parametrize("dim,n,parts,o,steps", [(2, (4097, 4097, 1), (2, 2, 1), 8, 4),
+                                                 (3, (257, 257, 257), (2, 2, 2), 6, 3)])
+def test_large_grids(dim, n, parts, o, steps):
+    """Large single requests: 2D subdomains of about 2050 columns (strips of
+    several bands across, staged by cp.async), large pitches and plane
+    strides; FP64 within 1e-11 and FP32 within 1e-5 of the oracle."""
+    p64 = W.Problem(dim=dim, n=n, monitor=W.ring_monitor(dim) if dim == 2 else W.shell_monitor(),
+                    parts=parts, overlap=o, dt=W.dt_for(n, dim, cfl=0.1 if dim == 2 else 0.05),
+                    tol=0.0, max_steps=steps, precision="fp64")
+    ref = oracle.solve(p64)
+    _check(p64, ref, psi=False)
+    _check(p64.replace(precision="fp32"), ref, psi=False)
+
+
 def test_config3_full_size_fp32_vs_oracle():
     """129^3 in 2x2x2 subdomains (overlap 6), FP32 sweep vs the FP64 oracle."""
     prob = W.config3("fp32", max_steps=25)
