@@ -388,6 +388,28 @@ def test_time_convergence_first_order():
         assert 0.85 <= slope <= 1.2, slope
 
 
+def test_space_convergence_second_order():
+    """Sect. 4.4 space study: the DD steady-state mesh converges at second
+    order in h (paper: slopes 1.85, 2.01, 1.99 in Linf, L1, L2).  Without a
+    finer reference, the order follows from three nested grids: the
+    differences 17->33 and 33->65 at the common nodes shrink by 2^p."""
+    gold = json.load(open(os.path.join(GOLD, "convergence_slopes.json")))
+    assert min(gold["space_slopes"].values()) > 1.7
+    xs = {}
+    for n in (17, 33, 65):
+        prob = W.Problem(dim=2, n=(n, n, 1), monitor=W.ring_monitor(), parts=(2, 2, 1),
+                         overlap=4, dt=W.dt_for((n, n, 1), 2), tol=1e-9, max_steps=10 ** 7)
+        r = oracle.solve(prob)
+        assert r.status == "ok"
+        s = (n - 1) // 16
+        xs[n] = r.x[:, ::s, ::s]
+    d1, d2 = xs[17] - xs[33], xs[33] - xs[65]
+    for norm in (lambda d: np.abs(d).sum(), lambda d: math.sqrt((d * d).sum()),
+                 lambda d: np.abs(d).max()):
+        order = math.log2(norm(d1) / norm(d2))
+        assert 1.7 <= order <= 2.3, order
+
+
 # ---------------------------------------------------------------- stop rule, variants
 
 def test_stop_rule_and_status():
