@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).  Problems are read by
 attribute (dim, n, lo, hi, monitor, parts, overlap, alternating, dt, tol,
-max_steps, stop_norm, stop_rule, check_every, rhs, normalize, lag_theta), so
+max_steps, stop_norm, stop_rule, check_every, rhs, normalize, lag_theta,
+exchange_every), so
 this module imports nothing from the product package.
 """
 from __future__ import annotations
@@ -56,7 +57,8 @@ class _Monitor(C.Structure):
 
 
 class _Decomp(C.Structure):
-    _fields_ = [("parts", C.c_int * 3), ("overlap", C.c_int), ("alternating", C.c_int)]
+    _fields_ = [("parts", C.c_int * 3), ("overlap", C.c_int), ("alternating", C.c_int),
+                ("exchange_every", C.c_int)]
 
 
 class _Params(C.Structure):
@@ -201,6 +203,7 @@ def solve(prob, psi0: Optional[np.ndarray] = None) -> OracleResult:
         d.parts[a] = int(prob.parts[a]) if a < prob.dim else 1
     d.overlap = int(prob.overlap)
     d.alternating = int(prob.alternating)
+    d.exchange_every = int(getattr(prob, "exchange_every", 1))
     p = _Params()
     p.dt, p.tol, p.max_steps = float(prob.dt), float(prob.tol), int(prob.max_steps)
     p.stop_norm, p.stop_rule = _NORM[prob.stop_norm], _RULE[prob.stop_rule]

@@ -19,7 +19,9 @@
  *      the normalised density of Eq. (edp);
  *   3. v^{n+1} = v^n + dt (G - c) at updated nodes;
  *   4. transmission nodes take the owner's v^n (parallel form) or, for an
- *      owner that precedes the subdomain, its v^{n+1} (Algorithm 1);
+ *      owner that precedes the subdomain, its v^{n+1} (Algorithm 1), at
+ *      every exchange step (every step, or every K-th with the interface
+ *      data frozen in between);
  *   5. residual per subdomain and the stop rule (Algorithm 1, steps 5-6;
  *      Eq. (dd_stop_criterion)).
  */
@@ -437,11 +439,11 @@ int or_solve(const or_grid *g, const or_monitor *m, const or_decomp *ddp,
              const or_params *p, const double *psi0, double *x_out,
              double *psi_out, double *res_hist, or_info *info) {
   dd_t d;
-  or_decomp one = {{1, 1, 1}, 0, 0};
+  or_decomp one = {{1, 1, 1}, 0, 0, 1};
   int rc, s, status = OR_NOT_CONVERGED, a;
   long n, steps = 0;
   double theta = 0.0, theta_prev = 0.0, last_res = INFINITY, min_det_last = INFINITY;
-  int check_every;
+  int check_every, exchange_every, exchange;
 
   if (!g || !m || !p || !x_out) return OR_ERR_INVALID;
   if (!(p->dt > 0.0) || p->max_steps < 0) return OR_ERR_INVALID;
@@ -452,6 +454,11 @@ int or_solve(const or_grid *g, const or_monitor *m, const or_decomp *ddp,
     return rc;
   }
   check_every = p->check_every > 0 ? p->check_every : 1;
+  if (ddp->exchange_every < 0) {
+    dd_free(&d);
+    return OR_ERR_INVALID;
+  }
+  exchange_every = ddp->exchange_every > 0 ? ddp->exchange_every : 1;
 
   /* Eq. (incond): Psi^0 = |xi|^2/2, i.e. v^0 = 0; or the warm start of
    * Sect. 2 (previous steady state) restricted to every subdomain.        */
@@ -554,7 +561,9 @@ int or_solve(const or_grid *g, const or_monitor *m, const or_decomp *ddp,
     }
     theta_prev = theta;
 
-    /* 4. transmission (Dirichlet) nodes from their owner */
+    /* 4. transmission (Dirichlet) nodes from their owner at an exchange
+     * step; between exchanges they keep the data of the last exchange    */
+    exchange = (n % exchange_every) == 0;
     for (s = 0; s < d.nsub; ++s) {
       sub_t *u = &d.sub[s];
       long i, j, l;
@@ -567,6 +576,10 @@ int or_solve(const or_grid *g, const or_monitor *m, const or_decomp *ddp,
             const sub_t *w;
             long ko;
             if (u->upd[k]) continue;
+            if (!exchange) {
+              u->vn[k] = u->v[k];
+              continue;
+            }
             o = owner_of(&d, gidx);
             w = &d.sub[o];
             ko = sidx(w, gidx[0] - w->lo[0], gidx[1] - w->lo[1], gidx[2] - w->lo[2]);

@@ -85,11 +85,17 @@ typedef struct {
 /* Overlapping decomposition (Sect. 3): parts[a] subdomains along axis a,
  * neighbours share `overlap` node indices.  alternating = 0 is the parallel
  * (Jacobi) transmission of Eq. (transmission_condition3); 1 is Algorithm 1,
- * where a subdomain takes the new value of an owner that precedes it.      */
+ * where a subdomain takes the new value of an owner that precedes it.
+ * exchange_every = K >= 1 (0 reads as 1): the interface data are exchanged
+ * at steps n = 0, K, 2K, ... only and stay frozen in between, the way the
+ * paper integrates each subdomain over an interval Delta tau with the
+ * neighbours' data of the interval's start (Sect. 3, the ode113 paragraph
+ * after Algorithm 1).  K = 1 is one exchange per step.                     */
 typedef struct {
   int parts[3];
   int overlap;
   int alternating;
+  int exchange_every;
 } or_decomp;
 
 enum { OR_STOP_MAX_UT = 0, OR_STOP_L2_INCREMENT = 1 };

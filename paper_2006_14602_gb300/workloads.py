@@ -78,6 +78,7 @@ class Problem:
     parts: Tuple[int, int, int] = (1, 1, 1)
     overlap: int = 0
     alternating: int = 0
+    exchange_every: int = 1
     dt: float = 1e-4
     tol: float = 1e-6
     max_steps: int = 2000

@@ -15,12 +15,19 @@ import pytest
 import oracle
 from oracle import oracle as _oracle_mod
 import test_oracle_pins as P
+import test_oracle_bruteforce as B
 
 SRC = os.path.join(os.path.dirname(_oracle_mod.__file__), "pma_oracle.c")
 
 # pins in rough order of cost; each mutant stops at the first that fails
 PINS = [
     ("monitor", P.test_monitor_closed_forms),
+    ("first_step", lambda: [P.test_first_step_from_identity_in_closed_form(d, r)
+                            for d in (1, 2, 3) for r in ("log", "root")]),
+    ("l2_norm", lambda: [P.test_l2_increment_residual_is_the_trapezoid_norm_of_the_step(d)
+                         for d in (1, 2, 3)]),
+    ("bruteforce", B.check_all),
+    ("alternating_order", P.test_alternating_transmission_takes_new_values_from_preceding_owners_only),
     ("quad1", lambda: P.test_operator_exact_on_quadratics(1)),
     ("quad2", lambda: P.test_operator_exact_on_quadratics(2)),
     ("quad3", lambda: P.test_operator_exact_on_quadratics(3)),
@@ -38,6 +45,8 @@ PINS = [
     ("overlap", P.test_dd_error_decreases_with_overlap),
     ("table", P.test_table_monitor_is_exact_on_multilinear_densities),
     ("alternating", lambda: P.test_dd_steady_state_equals_single_domain(1)),
+    ("exchange1", P.test_exchange_every_one_is_the_parallel_method),
+    ("frozen", P.test_frozen_interface_data_hold_between_exchanges),
 ]
 
 MUTANTS = {
@@ -74,6 +83,22 @@ MUTANTS = {
     "table_not_clamped": ("if (s > (double)(m->tn[a] - 1)) s = (double)(m->tn[a] - 1);",
                           ""),
     "table_cell_stride": ("stride[1] = m->tn[0];", "stride[1] = m->tn[1];"),
+    "l2_no_sqrt": ("if (p->stop_norm == OR_STOP_L2_INCREMENT) rs = sqrt(rs);", ""),
+    "l2_weights_not_halved": ("w *= (c3[a] == 0 || c3[a] == u->n[a] - 1) ? 0.5 * d.h[a] : d.h[a];",
+                              "w *= d.h[a];"),
+    "root_exponent_half": ("1.0 / (double)d.dim) - 1.0;", "0.5) - 1.0;"),
+    "root_theta_not_lagged": ("double th = (p->lag_theta ? theta_prev : theta);",
+                              "double th = theta;"),
+    "alternating_order": ("(ddp->alternating && o < s)", "(ddp->alternating && o > s)"),
+    "any_rule_is_max": ("last_res = (p->stop_rule == OR_RULE_ANY) ? rmin : rmax;",
+                        "last_res = rmax;"),
+    "normalisation_always_on": ("if (p->normalize == OR_NORM_GLOBAL_THETA) c = log(theta / d.vol);",
+                                "c = log(theta / d.vol);"),
+    "exchange_every_step": ("exchange = (n % exchange_every) == 0;", "exchange = 1;"),
+    "exchange_phase": ("exchange = (n % exchange_every) == 0;",
+                       "exchange = ((n + 1) % exchange_every) == 0;"),
+    "frozen_takes_owner": ("              u->vn[k] = u->v[k];\n              continue;",
+                           "              u->vn[k] = d.sub[owner_of(&d, gidx)].v[0];\n              continue;"),
 }
 
 

@@ -550,3 +550,167 @@ def test_tabulated_ring_converges_to_the_analytic_ring():
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert errs[2] < errs[1] < errs[0]
     assert 3.0 < r1 < 5.5 and 3.0 < r2 < 5.5, (errs, r1, r2)
+
+
+# ------------------------------------------------------------------ one step in closed form
+
+def _rho_np(mon, pts):
+    """Sum-of-terms density at points (n, dim) from the term shapes, numpy."""
+    r = np.full(pts.shape[0], float(mon.base))
+    for t in mon.terms:
+        q = ((pts - np.asarray(t.c[: pts.shape[1]])) ** 2).sum(1)
+        if t.type == "bump":
+            r += t.amp * np.exp(-t.width * q)
+        elif t.type == "ring":
+            r += t.amp * np.exp(-t.width * (q - t.r2) ** 2)
+        else:
+            raise ValueError(t.type)
+    return r
+
+
+def _trapezoid(prob):
+    """Trapezoid weights on the global grid, arrays (z, y, x)."""
+    ws = []
+    for a in range(prob.dim):
+        h = (prob.hi[a] - prob.lo[a]) / (prob.n[a] - 1)
+        w = np.full(prob.n[a], h)
+        w[[0, -1]] *= 0.5
+        ws.append(w)
+    W_ = ws[0]
+    for a in range(1, prob.dim):
+        W_ = np.multiply.outer(ws[a], W_)   # later axes are slower
+    return W_
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("rhs", ["log", "root"])
+def test_first_step_from_identity_in_closed_form(dim, rhs):
+    """From Psi^0 = |xi|^2/2 (Eq. incond) the mesh is the identity and
+    D^2 Psi = I at every node, so one forward-Euler step of Eq. (pmae) moves
+    Psi by dt log(|Omega_c| rho(xi)/theta) exactly, and the root form by
+    dt ((|Omega_c| rho(xi)/theta)^(1/d) - 1), with theta the trapezoid sum of
+    rho over the nodes (the normalisation of Eq. edp).  Single domain and
+    blocks alike: the transmission does not enter the first step."""
+    n = {1: 17, 2: 11, 3: 7}[dim]
+    lo, hi = (0.1, -0.2, 0.3), (1.2, 0.7, 1.1)
+    mon = W.Monitor("sum", 1.0, [W.Term("bump", 7.0, 9.0, 0.0, (0.5, 0.3, 0.6)),
+                                  W.Term("ring", 3.0, 20.0, 0.1, (0.7, 0.2, 0.8))])
+    nn = (n, n if dim > 1 else 1, n if dim > 2 else 1)
+    parts = {1: (2, 1, 1), 2: (2, 2, 1), 3: (2, 1, 2)}[dim]
+    for pr, o in (((1, 1, 1), 0), (parts, 3)):
+        prob = W.Problem(dim=dim, n=nn, lo=lo, hi=hi, monitor=mon, parts=pr, overlap=o,
+                         dt=1e-3, tol=0.0, max_steps=1, rhs=rhs)
+        r = oracle.solve(prob)
+        X = np.stack([g.T for g in np.meshgrid(*_xi(prob), indexing="ij")])
+        pts = X.reshape(dim, -1).T
+        rho = _rho_np(mon, pts).reshape(X.shape[1:])
+        vol = np.prod([hi[a] - lo[a] for a in range(dim)])
+        theta = (_trapezoid(prob) * rho).sum()
+        z = vol * rho / theta
+        F = np.log(z) if rhs == "log" else z ** (1.0 / dim) - 1.0
+        psi0 = 0.5 * (X ** 2).sum(0)
+        np.testing.assert_allclose(r.psi - psi0, 1e-3 * F, rtol=0, atol=1e-15)
+        assert abs(r.theta - theta) < 1e-12 * theta
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_l2_increment_residual_is_the_trapezoid_norm_of_the_step(dim):
+    """Eq. (dd_stop_criterion): on one domain the L2 residual of step k is
+    (sum_nodes w (Psi^{k+1} - Psi^k)^2)^(1/2) with the trapezoid weights of
+    Omega_c, taken here from two runs stopped after k and k + 1 steps."""
+    n = {1: 33, 2: 17, 3: 9}[dim]
+    prob = W.small_case(dim, n, steps=6).replace(stop_norm="l2_increment")
+    w = _trapezoid(prob)
+    for k in (0, 3, 5):
+        a = oracle.solve(prob.replace(max_steps=k)) if k else None
+        b = oracle.solve(prob.replace(max_steps=k + 1))
+        if a is None:
+            X = np.stack([g.T for g in np.meshgrid(*_xi(prob), indexing="ij")])
+            psi_k = 0.5 * (X ** 2).sum(0)
+        else:
+            psi_k = a.psi
+        want = math.sqrt((w * (b.psi - psi_k) ** 2).sum())
+        assert want > 0
+        assert abs(b.res[k] - want) <= 1e-9 * want, (k, b.res[k], want)
+
+
+def test_alternating_transmission_takes_new_values_from_preceding_owners_only():
+    """Algorithm 1 on two slabs: subdomain 1 takes subdomain 2's values of
+    the previous step (as in the parallel form, Eq. transmission_condition1)
+    and subdomain 2 takes subdomain 1's new values (Eq.
+    transmission_condition2).  From the identity the two forms agree after
+    one step; later (three steps: with overlap 4 a transmission value reaches
+    the neighbour's core after two more), the nodes owned by subdomain 1
+    still agree with the parallel run exactly, and only subdomain 2 differs.
+    (Without the global normalisation, as the subdomain equations of Eq.
+    pmae1a are printed: theta couples every node and would shift Psi
+    everywhere by a constant.)"""
+    base = W.Problem(dim=2, n=(21, 13, 1), monitor=W.ring_monitor(), parts=(2, 1, 1),
+                     overlap=4, dt=W.dt_for((21, 13, 1), 2), tol=0.0, max_steps=1,
+                     normalize="none")
+    _, _, clo, chi = oracle.extents(21, 2, 4)
+    for steps in (1, 3):
+        par = oracle.solve(base.replace(max_steps=steps))
+        alt = oracle.solve(base.replace(max_steps=steps, alternating=1))
+        own1 = (slice(None), slice(clo[0], chi[0] + 1))
+        own2 = (slice(None), slice(clo[1], chi[1] + 1))
+        np.testing.assert_array_equal(alt.psi[own1], par.psi[own1])
+        if steps == 1:
+            np.testing.assert_array_equal(alt.psi, par.psi)
+        else:
+            assert np.abs(alt.psi[own2] - par.psi[own2]).max() > 1e-9
+
+
+# ------------------------------------------------------------------ frozen interface data
+
+def test_exchange_every_one_is_the_parallel_method():
+    """K = 1 exchanges the interface data at every step: bitwise the same
+    run as the parallel form of Eq. (transmission_condition3)."""
+    prob = W.small_case(2, 25, parts=(2, 2, 1), overlap=4, steps=40)
+    a = oracle.solve(prob)
+    b = oracle.solve(prob.replace(exchange_every=1))
+    c = oracle.solve(prob.replace(exchange_every=0))
+    np.testing.assert_array_equal(a.x, b.x)
+    np.testing.assert_array_equal(a.x, c.x)
+    np.testing.assert_array_equal(a.res, b.res)
+
+
+def test_frozen_interface_data_lag_grows_with_the_interval_and_vanishes_at_steady_state():
+    """Interface data frozen over intervals of K steps (Sect. 3: each
+    subdomain is integrated over Delta tau with its neighbours' data of the
+    interval's start).  At a fixed pseudo time the DD mesh departs further
+    from the single-domain mesh as K grows; the steady state, a fixed point
+    of every exchange schedule under the global normalisation, is the
+    single-domain steady state for every K."""
+    base = W.Problem(dim=2, n=(33, 33, 1), monitor=W.ring_monitor(), dt=1e-4, tol=0.0,
+                     max_steps=400)
+    sd = oracle.solve(base)
+    errs = []
+    for K in (1, 2, 4, 8):
+        dd = oracle.solve(base.replace(parts=(2, 2, 1), overlap=4, exchange_every=K))
+        errs.append(np.abs(dd.x - sd.x).max())
+    assert all(a < b for a, b in zip(errs, errs[1:])), errs
+    steady = base.replace(tol=1e-10, max_steps=60000)
+    ref = oracle.solve(steady)
+    for K in (2, 8):
+        dd = oracle.solve(steady.replace(parts=(2, 2, 1), overlap=4, exchange_every=K,
+                                         check_every=K))
+        assert dd.status == "ok" and np.abs(dd.x - ref.x).max() < 1e-7
+
+
+def test_frozen_interface_data_hold_between_exchanges():
+    """Between exchanges a subdomain sees constant Dirichlet data.  With
+    K = 5 the first exchange after step 0 is at step 5 (it writes the
+    Dirichlet values of Psi^6), so up to that point the run equals the one
+    with K = 10; the new data reach the owned cores (two nodes inside the
+    Dirichlet layer at overlap 4) two steps later, at Psi^8.  Unnormalised
+    subdomain equations (Eq. pmae1a), so that no global constant couples the
+    subdomains."""
+    prob = W.small_case(2, 25, parts=(2, 2, 1), overlap=4, steps=8).replace(normalize="none")
+    for steps in range(1, 9):
+        a = oracle.solve(prob.replace(max_steps=steps, exchange_every=5))
+        b = oracle.solve(prob.replace(max_steps=steps, exchange_every=10))
+        if steps <= 7:
+            np.testing.assert_array_equal(a.psi, b.psi)
+        else:
+            assert np.abs(a.psi - b.psi).max() > 0
