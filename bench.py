@@ -51,6 +51,14 @@ WORKLOADS = {
           "2000 steps, all 32 subdomains in one launch",
     "c3": "3D 129^3 in 2x2x2 subdomains (overlap 6), spherical shell monitor, FP32 sweep, "
           "FP64 residual/stop test, 2000 steps",
+    "c3x16": "3D: 16 requests of 129^3 in 2x2x2 subdomains (overlap 6), spherical shell "
+             "monitor, FP32 sweep, FP64 residual/stop test, 2000 steps; 315 MB of state "
+             "(larger than L2)",
+    "c3big": "3D 257^3 in 4x4x4 subdomains (overlap 6), spherical shell monitor, FP32 sweep, "
+             "FP64 residual/stop test, 2000 steps; 166 MB of state (larger than L2)",
+    "c4x2": "uneven batch twice over: 1024 independent 2D problems (seeds 14602 and 14603), "
+            "sides log-uniform in [17,513], 1-16 subdomains (overlap 4-8), 1-4 Gaussian "
+            "bumps/rings, FP32, tol 1e-6 or 2000 steps; 197 MB of state (larger than L2)",
 }
 
 
@@ -148,6 +156,15 @@ def make_workload(name: str, precision: str, max_steps=None):
         probs = [W.config2("ring", precision), W.config2("sine", precision)]
     elif name == "c3":
         probs = [W.config3(precision)]
+    elif name == "c3x16":
+        probs = [W.config3(precision) for _ in range(16)]
+    elif name == "c3big":
+        n = (257, 257, 257)
+        probs = [W.config3(precision).replace(n=n, parts=(4, 4, 4),
+                                              dt=W.dt_for(n, 3, cfl=0.05))]
+    elif name == "c4x2":
+        probs = (W.config4(precision=precision) +
+                 W.config4(seed=W.MASTER_SEED + 1, precision=precision))
     else:
         raise SystemExit("unknown workload %s" % name)
     if max_steps is not None:

@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define PMA_ABI_VERSION 1
+#define PMA_ABI_VERSION 2
 #define PMA_MAX_TERMS 4
 #define PMA_MAX_PARTS 32 /* subdomains per axis */
 
@@ -123,13 +123,21 @@ typedef struct {
  * transmission: PMA_TRANSMISSION_PARALLEL (Eq. transmission_condition3,
  * every subdomain takes its neighbours' previous-step values) or
  * PMA_TRANSMISSION_ALTERNATING (Algorithm 1: a subdomain takes the new value
- * of an owner that precedes it in raster order).                           */
+ * of an owner that precedes it in raster order).
+ * exchange_every: K >= 1 (0 reads as 1).  The subdomains exchange interface
+ * data at steps 0, K, 2K, ... only; in between, every transmission node keeps
+ * the value of the last exchange, as when each subdomain is integrated over
+ * a pseudo-time interval with its neighbours' data frozen at the interval's
+ * start (Sect. 3, the paragraph after Algorithm 1).  K = 1 is one exchange
+ * per step (bitwise the K = 1 behaviour of either transmission form).
+ * Negative values are rejected with PMA_ERR_INVALID.                       */
 enum { PMA_TRANSMISSION_PARALLEL = 0, PMA_TRANSMISSION_ALTERNATING = 1 };
 
 typedef struct {
   int32_t parts[3];
   int32_t overlap;
   int32_t transmission;
+  int32_t exchange_every;
 } pma_decomp;
 
 /* Pseudo-time integration and stopping (Sects. 2, 4.4).
@@ -209,7 +217,8 @@ pma_status pma_destroy(pma_ctx *ctx);
  *   PMA_OPT_TILE_2D        2D tile shape id (0 = auto)
  *   PMA_OPT_TILE_3D        3D tile shape id (0 = auto)
  *   PMA_OPT_MAX_ACTIVE     cap on concurrently admitted requests (0 = none)
- *   PMA_OPT_RESIDENT       k > 0: 2D requests of at most 16 subdomains whose
+ *   PMA_OPT_RESIDENT       k > 0: 2D requests of at most 16 subdomains (parallel
+ *                          transmission, one exchange per step) whose
  *                          subdomains fit the first k shared-memory classes
  *                          (24, 56, 112, 220 KiB per subdomain) run
  *                          cluster-resident: one CTA per subdomain for a whole
@@ -376,13 +385,15 @@ pma_status pma_solve(int device, const pma_grid *grid, const pma_monitor *monito
  *   cuda_stream  stream to run on (NULL: the legacy default stream); the
  *              call returns after the stream has finished its work.
  * Requests whose state, tables and records do not fit the scratch area are
- * rejected with PMA_ERR_NOMEM (pma_last_error gives the bytes needed); the
- * transmission must be PMA_TRANSMISSION_PARALLEL.  Every call shares the
- * same scratch area: calls that overlap on the GPU (two streams, two host
- * threads, or a call racing a previous call still in flight on another
- * stream) corrupt each other.  The first call on a device also performs a
- * one-time set-up (it looks up the scratch area's device address), so make
- * the first call on each device before any stream capture begins.
+ * rejected with PMA_ERR_NOMEM (pma_last_error gives the bytes needed).  Both
+ * transmission forms and every exchange_every are accepted.  Every call
+ * shares the same scratch area: calls that overlap on the GPU (two streams,
+ * two host threads, or a call racing a previous call still in flight on
+ * another stream) corrupt each other.  Each call looks up the scratch area's
+ * device address on the current device (so a device reset between calls
+ * is harmless); the first call on a device also loads the library's device
+ * code there, so make the first call on each device before any stream
+ * capture begins.
  * Returns the request's final status (PMA_OK, PMA_NOT_CONVERGED,
  * PMA_ERR_TANGLED) or an error.                                             */
 #define PMA_STATIC_SCRATCH_BYTES (32u << 20)

@@ -6,8 +6,8 @@ does.  It wraps the plain C implementation in ``pma_oracle.c`` (built with
 ``build()``) and shares no code with the CUDA library: problem descriptions
 are read by attribute from the seeded input module, nothing else is shared.
 """
-from .oracle import (build, lib_path, solve, operator, monitor_eval, extents,
-                     quality, OracleResult)
+from .oracle import (build, lib_path, solve, solve_parallel, operator, monitor_eval,
+                     extents, quality, OracleResult)
 
-__all__ = ["build", "lib_path", "solve", "operator", "monitor_eval", "extents",
+__all__ = ["build", "lib_path", "solve", "solve_parallel", "operator", "monitor_eval", "extents",
            "quality", "OracleResult"]

@@ -276,3 +276,26 @@ def quality(prob, psi: np.ndarray) -> dict:
         raise ValueError("quality failed")
     return {"E2": out[0], "Emax": out[1], "min_det": out[2], "min_cell": out[3],
             "theta": out[4]}
+
+
+def _solve_job(args):
+    prob, psi0 = args
+    return solve(prob, psi0)
+
+
+def solve_parallel(probs, workers: Optional[int] = None, psi0s=None):
+    """Run the oracle on several problems at once, one spawned process per
+    problem (at most `workers`, default the host's cores up to 16); returns
+    the results in order.  Spawned (not forked) workers, so it is safe in a
+    process that already uses a GPU."""
+    import multiprocessing as mp
+    build()
+    probs = list(probs)
+    if psi0s is None:
+        psi0s = [None] * len(probs)
+    n = max(1, min(len(probs), workers or min(os.cpu_count() or 1, 16)))
+    if n == 1:
+        return [solve(p, q) for p, q in zip(probs, psi0s)]
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.map(_solve_job, list(zip(probs, psi0s)), chunksize=1)
+

@@ -188,6 +188,10 @@ pma_status build_request(Request& r) {
     set_err("decomp.transmission: unknown form");
     return PMA_ERR_INVALID;
   }
+  if (r.d.exchange_every < 0) {
+    set_err("decomp.exchange_every must be >= 0 (0 and 1: every step)");
+    return PMA_ERR_INVALID;
+  }
   if (!monitor_ok(r.m, r.dim)) {
     set_err("monitor: bad kind, term or axis");
     return PMA_ERR_INVALID;
@@ -449,6 +453,7 @@ void fill_probdesc(const Request& r, ProbDesc& pd) {
   pd.rhs = r.p.rhs;
   pd.normalize = r.p.normalize;
   pd.transmission = r.d.transmission;
+  pd.exchange_every = r.d.exchange_every > 1 ? r.d.exchange_every : 1;
   pd.dt = r.p.dt;
   pd.tol = r.p.tol;
   pd.max_steps = r.p.max_steps;
@@ -470,6 +475,7 @@ void fill_hot(const Request& r, const ProbDesc& pd, ProbHot<T>& h) {
   h.sub_base = pd.sub_base;
   h.ntiles = pd.tile_end - pd.tile_begin;
   h.alternating = pd.transmission == PMA_TRANSMISSION_ALTERNATING ? 1 : 0;
+  h.exchange_every = pd.exchange_every;
   for (int a = 0; a < 3; ++a) {
     h.N[a] = pd.N[a];
     h.parts[a] = pd.parts[a];
@@ -866,6 +872,7 @@ int pick_res_class(const pma_ctx* c, const Request& r, int* smem) {
   *smem = 0;
   if (!c->opt_resident || c->launch_mode != PMA_LAUNCH_BATCHED || r.dim != 2) return -1;
   if (r.d.transmission != PMA_TRANSMISSION_PARALLEL) return -1;
+  if (r.d.exchange_every > 1) return -1;
   const int nsub = (int)r.subs.size();
   if (nsub > kResClusterMax) return -1;
   int need = 0;
@@ -1856,29 +1863,23 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_static_scratch[PMA_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxStaticDevices = 64;
-std::mutex g_static_mu;
-void* g_static_ptr[kMaxStaticDevices] = {};
-
 // Device address of the scratch array on device `dev` (current).  In host
-// code the array's name is only a stand-in, so the address is looked up
-// once per device and cached.
+// code the array's name is only a stand-in, so the address is looked up on
+// every call: after a device reset, or when the primary context is released
+// and created again, the module is loaded anew and the array may sit at a
+// new address, so a cached pointer could go stale.
 pma_status static_scratch(int dev, void** out) {
-  if (dev < 0 || dev >= kMaxStaticDevices) {
-    set_err("pma_solve_static: device index out of range");
+  if (dev < 0) {
+    set_err("pma_solve_static: no current device");
     return PMA_ERR_INVALID;
   }
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) {
-      set_err(std::string("pma_solve_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      return PMA_ERR_CUDA;
-    }
-    g_static_ptr[dev] = p;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p) {
+    set_err(std::string("pma_solve_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    return PMA_ERR_CUDA;
   }
-  *out = g_static_ptr[dev];
+  *out = p;
   return PMA_OK;
 }
 

@@ -69,7 +69,7 @@ struct alignas(16) ProbHot {
   int alternating;  // 1: alternating transmission (Algorithm 1)
   int mon_fast;     // 1: sum of bump / ring terms (the packed monitor path)
   int nb_base;      // first neighbour entry of the problem's subdomains
-  int pad1;
+  int exchange_every;  // K >= 1: interface data exchanged at steps 0, K, 2K, ...
   T lo[3], h[3], inv2h[3], invh2[3], inv4hh[3], hw[3];
   T dt, vol;
   double hd[3];
@@ -89,7 +89,7 @@ struct ProbDesc {
   int tile_begin, tile_end;     // range in this problem's class work list
   int cls;
   int stop_norm, stop_rule, check_every, rhs, normalize, transmission;
-  int pad0;
+  int exchange_every;           // K >= 1 (frozen interface data between exchanges)
   double dt, tol;
   long long max_steps;
   const double* psi0;           // optional warm start (global grid), device
@@ -108,6 +108,13 @@ struct alignas(16) SubDesc {
   int pitch;         // row stride in elements (n[0] rounded up to 4)
   void* v[2];        // ping-pong state buffers, pitch * n[1] * n[2] values
 };
+
+// Step n (the step that computes v^{n+1}) exchanges interface data when
+// n is a multiple of K; between exchanges a transmission node keeps the value
+// it was staged with.
+__host__ __device__ inline bool exchange_step(long long n, int K) {
+  return K <= 1 || (n >= 0 && n % K == 0);
+}
 
 struct alignas(16) ProbState {
   long long step;       // forward-Euler steps taken

@@ -420,6 +420,60 @@ __device__ void stage_alternating(const LaunchArgs& a, const SmemHdr<T>& S, T* s
   }
 }
 
+// Transmission nodes of a 3D box [i0, i0+cols) x [j0, j0+rows) x [k0,
+// k0+depth) in a fixed enumeration: whole transmission planes, then in the
+// other planes the transmission rows and the transmission columns of the
+// remaining rows (each node once).
+struct TrBox3 {
+  int kp0, kp1, jr0, jr1, ic0, ic1;
+  int npl, plane_e, nrow_e, per_plane, total;
+  // node e (0 <= e < total); false for an entry already counted elsewhere
+  __device__ __forceinline__ bool node(int e, int i0, int j0, int k0, int cols, int rows,
+                                       int& i, int& j, int& kk) const {
+    if (e < npl * plane_e) {
+      const int q = e >= plane_e ? 1 : 0, rem = e - q * plane_e;
+      kk = (q == 0 && kp0 >= 0) ? kp0 : kp1;
+      const int rr = rem / cols;
+      j = j0 + rr;
+      i = i0 + rem - rr * cols;
+      return true;
+    }
+    const int e2 = e - npl * plane_e, l = e2 / per_plane;
+    kk = k0 + l;
+    if (kk == kp0 || kk == kp1) return false;  // done with its plane
+    const int e3 = e2 - l * per_plane;
+    if (e3 < nrow_e) {
+      const int q = e3 >= cols ? 1 : 0;
+      j = (q == 0 && jr0 >= 0) ? jr0 : jr1;
+      i = i0 + e3 - q * cols;
+      return true;
+    }
+    const int e4 = e3 - nrow_e, q = e4 >= rows ? 1 : 0;
+    i = (q == 0 && ic0 >= 0) ? ic0 : ic1;
+    j = j0 + e4 - q * rows;
+    return !(j == jr0 || j == jr1);  // corner: done with its row
+  }
+};
+__device__ __forceinline__ TrBox3 tr_box3(int dlx, int dhx, int dly, int dhy, int dlz, int dhz,
+                                          int i0, int j0, int k0, int cols, int rows,
+                                          int depth) {
+  TrBox3 t;
+  t.kp0 = (dlz >= k0 && dlz < k0 + depth) ? dlz : -1;
+  t.kp1 = (dhz >= k0 && dhz < k0 + depth) ? dhz : -1;
+  t.jr0 = (dly >= j0 && dly < j0 + rows) ? dly : -1;
+  t.jr1 = (dhy >= j0 && dhy < j0 + rows) ? dhy : -1;
+  t.ic0 = (dlx >= i0 && dlx < i0 + cols) ? dlx : -1;
+  t.ic1 = (dhx >= i0 && dhx < i0 + cols) ? dhx : -1;
+  t.npl = (t.kp0 >= 0 ? 1 : 0) + (t.kp1 >= 0 ? 1 : 0);
+  const int nrw = (t.jr0 >= 0 ? 1 : 0) + (t.jr1 >= 0 ? 1 : 0);
+  const int ncl = (t.ic0 >= 0 ? 1 : 0) + (t.ic1 >= 0 ? 1 : 0);
+  t.plane_e = rows * cols;
+  t.nrow_e = nrw * cols;
+  t.per_plane = t.nrow_e + ncl * rows;
+  t.total = t.npl * t.plane_e + depth * t.per_plane;
+  return t;
+}
+
 // ---------------------------------------------------------------- work queue
 // Persistent CTAs pull work items from a per-launch counter; the last CTA
 // to run out resets the counters for the next launch.  The partial record
@@ -989,16 +1043,19 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
       // Transmission nodes of the band (Eq. transmission_condition3): whole
       // transmission rows, then the transmission columns of the other rows,
       // one node per thread, while the staging copies are in flight (the
-      // main loop does not store these nodes).
-      if (phase == PH_RUN) {
-        const int jr0 = (dly >= j0 && dly < j0 + rows) ? dly : -1;
-        const int jr1 = (dhy >= j0 && dhy < j0 + rows) ? dhy : -1;
-        const int ic0 = (dlx >= i0 && dlx < i0 + cols) ? dlx : -1;
-        const int ic1 = (dhx >= i0 && dhx < i0 + cols) ? dhx : -1;
-        const int nrw = (jr0 >= 0 ? 1 : 0) + (jr1 >= 0 ? 1 : 0);
-        const int ncl = (ic0 >= 0 ? 1 : 0) + (ic1 >= 0 ? 1 : 0);
-        const int nrow_e = nrw * cols;
-        const int total = nrow_e + ncl * rows;
+      // main loop does not store these nodes).  At a step without exchange
+      // (exchange_every > 1) the nodes keep their staged values instead,
+      // copied once the band has landed (after S2).
+      const int jr0 = (dly >= j0 && dly < j0 + rows) ? dly : -1;
+      const int jr1 = (dhy >= j0 && dhy < j0 + rows) ? dhy : -1;
+      const int ic0 = (dlx >= i0 && dlx < i0 + cols) ? dlx : -1;
+      const int ic1 = (dhx >= i0 && dhx < i0 + cols) ? dhx : -1;
+      const int nrow_e = ((jr0 >= 0 ? 1 : 0) + (jr1 >= 0 ? 1 : 0)) * cols;
+      const int tr_total = nrow_e + ((ic0 >= 0 ? 1 : 0) + (ic1 >= 0 ? 1 : 0)) * rows;
+      const int kex = H.ph.exchange_every;
+      const bool exch = exchange_step(H.ps.step, kex);
+      if (phase == PH_RUN && exch) {
+        const int total = tr_total;
         const NbEnt* const nbi = item_nb<T, 2>(a, H);
         for (int e0 = tid; e0 < total; e0 += 2 * NT) {
           // two nodes per thread and pass: both owner loads before the stores
@@ -1092,11 +1149,30 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2
           }
         }
       }
-      if (H.ph.alternating) {
+      if (H.ph.alternating && exchange_step(H.ps.step - 1, kex)) {
         __syncthreads();
         stage_alternating<T, NT>(a, H, sv, SWp, SH, 1, i0, j0, 0, cols);
       }
       __syncthreads();  // S2: band staged
+      if (phase == PH_RUN && !exch) {
+        // interface data frozen between exchanges: every transmission node
+        // of the band keeps the value it was staged with (offset included)
+        for (int e = tid; e < tr_total; e += NT) {
+          int i, j;
+          if (e < nrow_e) {
+            const int q = e >= cols ? 1 : 0;
+            j = (q == 0 && jr0 >= 0) ? jr0 : jr1;
+            i = i0 + e - q * cols;
+          } else {
+            const int e2 = e - nrow_e;
+            const int q = e2 >= rows ? 1 : 0;
+            i = (q == 0 && ic0 >= 0) ? ic0 : ic1;
+            j = j0 + e2 - q * rows;
+            if (j == jr0 || j == jr1) continue;  // corner: done with its row
+          }
+          st_global(dst + j * pitch + i, sv[(j - j0 + 1) * SWp + (i - i0 + 4)]);
+        }
+      }
       const T h0 = H.ph.h[0], h1 = H.ph.h[1];
       const T hw0 = H.ph.hw[0], hw1 = H.ph.hw[1];
       const int N0 = H.ph.N[0], N1 = H.ph.N[1];
@@ -1715,44 +1791,17 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
       // Transmission nodes of the box (Eq. transmission_condition3), one
       // per thread while the staging copies are in flight: whole
       // transmission planes, then in the other planes the transmission rows
-      // and the transmission columns of the remaining rows.
-      if (phase == PH_RUN) {
-        const int kp0 = (dlz >= k0 && dlz < k0 + depth) ? dlz : -1;
-        const int kp1 = (dhz >= k0 && dhz < k0 + depth) ? dhz : -1;
-        const int jr0 = (dly >= j0 && dly < j0 + rows) ? dly : -1;
-        const int jr1 = (dhy >= j0 && dhy < j0 + rows) ? dhy : -1;
-        const int ic0 = (dlx >= i0 && dlx < i0 + cols) ? dlx : -1;
-        const int ic1 = (dhx >= i0 && dhx < i0 + cols) ? dhx : -1;
-        const int npl = (kp0 >= 0 ? 1 : 0) + (kp1 >= 0 ? 1 : 0);
-        const int nrw = (jr0 >= 0 ? 1 : 0) + (jr1 >= 0 ? 1 : 0);
-        const int ncl = (ic0 >= 0 ? 1 : 0) + (ic1 >= 0 ? 1 : 0);
-        const int plane_e = rows * cols, nrow_e = nrw * cols, per_plane = nrow_e + ncl * rows;
-        const int total = npl * plane_e + depth * per_plane;
+      // and the transmission columns of the remaining rows.  At a step
+      // without exchange (exchange_every > 1) they keep their staged values
+      // instead, copied once the box has landed.
+      const int kex = H.ph.exchange_every;
+      const bool exch = exchange_step(H.ps.step, kex);
+      const TrBox3 tb = tr_box3(dlx, dhx, dly, dhy, dlz, dhz, i0, j0, k0, cols, rows, depth);
+      if (phase == PH_RUN && exch) {
         const NbEnt* const nbi = item_nb<T, 3>(a, H);
-        for (int e = tid; e < total; e += NT) {
+        for (int e = tid; e < tb.total; e += NT) {
           int i, j, kk;
-          if (e < npl * plane_e) {
-            const int q = e >= plane_e ? 1 : 0, rem = e - q * plane_e;
-            kk = (q == 0 && kp0 >= 0) ? kp0 : kp1;
-            const int rr = rem / cols;
-            j = j0 + rr;
-            i = i0 + rem - rr * cols;
-          } else {
-            const int e2 = e - npl * plane_e, l = e2 / per_plane;
-            kk = k0 + l;
-            if (kk == kp0 || kk == kp1) continue;  // done with its plane
-            const int e3 = e2 - l * per_plane;
-            if (e3 < nrow_e) {
-              const int q = e3 >= cols ? 1 : 0;
-              j = (q == 0 && jr0 >= 0) ? jr0 : jr1;
-              i = i0 + e3 - q * cols;
-            } else {
-              const int e4 = e3 - nrow_e, q = e4 >= rows ? 1 : 0;
-              i = (q == 0 && ic0 >= 0) ? ic0 : ic1;
-              j = j0 + e4 - q * rows;
-              if (j == jr0 || j == jr1) continue;  // corner: done with its row
-            }
-          }
+          if (!tb.node(e, i0, j0, k0, cols, rows, i, j, kk)) continue;
           st_global(dst + kk * ppitch + j * pitch + i, gather_owner<T, 3>(nbi, H, i, j, kk));
         }
       }
@@ -1840,7 +1889,7 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
           }
         }
       }
-      if (H.ph.alternating) {
+      if (H.ph.alternating && exchange_step(H.ps.step - 1, kex)) {
         __syncthreads();
         stage_alternating<T, NT>(a, H, sv, SWp, SHY, SHZ, i0, j0, k0, cols);
       }
@@ -1874,6 +1923,16 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
         kcol[c] = upd ? T(0) : big_val<T>();
       }
       __syncthreads();  // box staged
+      if (phase == PH_RUN && !exch) {
+        // interface data frozen between exchanges: every transmission node
+        // of the box keeps the value it was staged with (offset included)
+        for (int e = tid; e < tb.total; e += NT) {
+          int i, j, kk;
+          if (!tb.node(e, i0, j0, k0, cols, rows, i, j, kk)) continue;
+          st_global(dst + kk * ppitch + j * pitch + i,
+                    sv[(kk - k0 + 1) * PS + (j - j0 + 1) * SWp + (i - i0 + 4)]);
+        }
+      }
       RunAcc<T> A = RunAcc<T>::zero();
       const P2<T> DT2 = K.DT2;
       const P2<T> M2 = P2<T>::s(T(-2)), ONE = P2<T>::s(T(1));
@@ -2319,18 +2378,19 @@ cudaError_t launch_res2d(bool fp64, int id, const ResArgs& a, int nclusters, int
 // subdomain whose core holds it (mirror ghost on faces of Omega_c, i.e.
 // x_a = xi_a on faces normal to a), and Psi = v - S + |xi|^2/2.
 // A transmission node carries the previous step's offset (corr is added),
-// except under alternating transmission when its owner precedes the
-// subdomain: then the owner's current value is the node's value.
+// except under alternating transmission after an exchange step when its
+// owner precedes the subdomain (alt_new): then the owner's current value is
+// the node's value.
 template <typename T>
 __device__ __forceinline__ T fetch_v(const SubDesc& sd, const T* v, int dim, int i, int j, int l,
                                      double corr, const ProbDesc& pd, const SubDesc* subs,
-                                     int parity) {
+                                     int parity, bool alt_new) {
   const int n0 = sd.n[0], n1 = sd.n[1], n2 = sd.n[2];
   i = reflect_clamp(i, n0, sd.faces & 1, sd.faces & 2);
   j = dim > 1 ? reflect_clamp(j, n1, sd.faces & 4, sd.faces & 8) : 0;
   l = dim > 2 ? reflect_clamp(l, n2, sd.faces & 16, sd.faces & 32) : 0;
   if (is_dir(sd.faces, dim, i, j, l, n0, n1, n2)) {
-    if (pd.transmission == PMA_TRANSMISSION_ALTERNATING) {
+    if (alt_new) {
       const int kx = sd.k[0] + (i < sd.clo[0] ? -1 : (i > sd.chi[0] ? 1 : 0));
       const int ky = sd.k[1] + (j < sd.clo[1] ? -1 : (j > sd.chi[1] ? 1 : 0));
       const int kz = sd.k[2] + (l < sd.clo[2] ? -1 : (l > sd.chi[2] ? 1 : 0));
@@ -2365,6 +2425,8 @@ __device__ void combine_node(const CombineJob& J, long long g, const SubDesc* su
   const int i = gi - sd.g0[0], j = gj - sd.g0[1], l = gl - sd.g0[2];
   const int gg[3] = {gi, gj, gl};
   const int li[3] = {i, j, l};
+  const bool alt = pd.transmission == PMA_TRANSMISSION_ALTERNATING &&
+                   exchange_step(ps.step - 1, pd.exchange_every);
   double q = 0.0;
   for (int a = 0; a < dim; ++a) {
     const double xi = pd.lo[a] + (double)gg[a] * pd.h[a];
@@ -2374,8 +2436,8 @@ __device__ void combine_node(const CombineJob& J, long long g, const SubDesc* su
       int p[3] = {li[0], li[1], li[2]}, m[3] = {li[0], li[1], li[2]};
       p[a] += 1;
       m[a] -= 1;
-      const T vp = fetch_v<T>(sd, v, dim, p[0], p[1], p[2], ps.corr, pd, subs, ps.parity);
-      const T vm = fetch_v<T>(sd, v, dim, m[0], m[1], m[2], ps.corr, pd, subs, ps.parity);
+      const T vp = fetch_v<T>(sd, v, dim, p[0], p[1], p[2], ps.corr, pd, subs, ps.parity, alt);
+      const T vm = fetch_v<T>(sd, v, dim, m[0], m[1], m[2], ps.corr, pd, subs, ps.parity, alt);
       xa = xi + (double)(vp - vm) * (0.5 / pd.h[a]);
     }
     if (J.out_fp64)
@@ -2455,9 +2517,11 @@ __device__ void node_x_and_hessian(const SubDesc* subs, const ProbDesc& pd, cons
   const SubDesc& sd = subs[pd.sub_base + (kk[2] * pd.parts[1] + kk[1]) * pd.parts[0] + kk[0]];
   const T* v = (const T*)sd.v[ps.parity];
   const int li[3] = {gg[0] - sd.g0[0], gg[1] - sd.g0[1], gg[2] - sd.g0[2]};
+  const bool alt = pd.transmission == PMA_TRANSMISSION_ALTERNATING &&
+                   exchange_step(ps.step - 1, pd.exchange_every);
   auto f = [&](int di, int dj, int dl) -> double {
     return (double)fetch_v<T>(sd, v, dim, li[0] + di, li[1] + dj, li[2] + dl, ps.corr, pd, subs,
-                              ps.parity);
+                              ps.parity, alt);
   };
   const double vc = f(0, 0, 0);
   int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};

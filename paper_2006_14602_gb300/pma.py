@@ -82,7 +82,7 @@ class pma_monitor(C.Structure):
 
 class pma_decomp(C.Structure):
     _fields_ = [("parts", C.c_int32 * 3), ("overlap", C.c_int32),
-                ("transmission", C.c_int32)]
+                ("transmission", C.c_int32), ("exchange_every", C.c_int32)]
 
 
 class pma_params(C.Structure):
@@ -364,6 +364,7 @@ def to_structs(prob):
         d.parts[a] = int(prob.parts[a]) if a < prob.dim else 1
     d.overlap = int(prob.overlap)
     d.transmission = int(prob.alternating)
+    d.exchange_every = int(getattr(prob, "exchange_every", 1))
     p = pma_params()
     p.dt, p.tol, p.max_steps = float(prob.dt), float(prob.tol), int(prob.max_steps)
     p.stop_norm, p.stop_rule = _NORM[prob.stop_norm], _RULE[prob.stop_rule]

@@ -50,6 +50,7 @@ int main(void) {
          sizeof(pma_monitor), sizeof(pma_decomp), sizeof(pma_params), sizeof(pma_info));
   F(pma_grid, lo) F(pma_grid, hi) F(pma_term, amp) F(pma_term, c)
   F(pma_monitor, base) F(pma_monitor, term) F(pma_decomp, overlap)
+  F(pma_decomp, exchange_every)
   F(pma_params, max_steps) F(pma_params, precision) F(pma_info, status)
   F(pma_info, latency_us)
   return 0;
@@ -76,7 +77,7 @@ def test_struct_layout_matches_header():
 
 
 def test_status_strings_and_version(lib):
-    assert pma.pma_abi_version() == 1
+    assert pma.pma_abi_version() == 2
     assert pma.pma_status_str(pma.PMA_ERR_TANGLED) == "mesh tangled"
     assert pma.pma_status_str(12345) == "unknown status"
     assert isinstance(pma.pma_last_error(), str)
