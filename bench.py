@@ -128,7 +128,10 @@ def serving(args):
     small = run(stream_at(rates[-1] if args.rate else sat["meshes_per_s"]), "fp32", False,
                 budget=args.budget_mb << 20)
     small["budget_mb"] = args.budget_mb
-    plain = run(stream_at(1e9)[: args.plain_requests], "fp64", True) if args.plain_requests else None
+    full = stream_at(1e9)
+    plain_n = len(full) if args.plain_requests < 0 else args.plain_requests
+    plain = run(full[:plain_n], "fp64", True) if plain_n else None
+    same = run(full[:plain_n], "fp32", False) if plain_n and plain_n != len(full) else sat
     line = {
         "metric": "meshes/s (serving stream)", "value": sat["meshes_per_s"], "unit": "meshes/s",
         "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -144,6 +147,8 @@ def serving(args):
         "poisson_sweep": sweep,
         "small_budget": small,
         "plain_fp64_per_subdomain": plain,
+        "batched_fp32_same_requests": same,
+        "budget_gb": 120,
     }
     print(json.dumps(line))
     return 0
@@ -364,7 +369,10 @@ def native(args, rank, world, device):
     offs = np.concatenate([[0], np.cumsum(nodes_out)])[:-1]
     ptrs = [out.data_ptr() + 8 * int(o) for o in offs]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    # end-to-end leg: the requests as the C structs a caller hands to
+    # pma_submit, and one page-locked host buffer that receives every mesh
     host_out = torch.empty(sum(nodes_out), dtype=torch.float64, pin_memory=True)
+    structs = [pma.to_structs(p) for p in probs]
 
     def one_step(timed_events: bool):
         ids = [ctx.submit(p) for p in probs]
@@ -391,22 +399,25 @@ def native(args, rank, world, device):
         return e0.elapsed_time(e1), stats, infos
 
     def e2e_step():
-        # public API from host structs to host meshes, copies included
+        # the C ABI from host structs to host meshes: pma_submit (inputs
+        # copied), pma_run (admission uploads the tables, then every step),
+        # pma_get_mesh_batch (one combination and one device-to-host copy of
+        # every mesh into the page-locked host buffer); wall clock around it
         torch.cuda.synchronize(device)
         pma.pma_get_stats(ctx.h, 1)
         t0 = time.perf_counter()
-        ids = [ctx.submit(p) for p in probs]
+        ids = []
+        for g, m, d, p in structs:
+            st, rid = pma.pma_submit(ctx.h, g, m, d, p, None)
+            if st != pma.PMA_OK:
+                raise pma.PmaError("pma_submit", st)
+            ids.append(rid)
         ctx.run()
-        st = pma.pma_get_mesh_device_batch(ctx.h, ids, ptrs, 1)
+        st = pma.pma_get_mesh_batch(ctx.h, ids, host_out.data_ptr())
         if st != pma.PMA_OK:
-            raise pma.PmaError("pma_get_mesh_device_batch", st)
-        with torch.cuda.stream(stream):
-            host_out.copy_(out, non_blocking=True)
-        stream.synchronize()
+            raise pma.PmaError("pma_get_mesh_batch", st)
         t1 = time.perf_counter()
         _, stats = pma.pma_get_stats(ctx.h, 1)
-        for i in ids:
-            pma.pma_release(ctx.h, i)
         return (t1 - t0) * 1e3, stats
 
     for _ in range(args.warmup):
@@ -447,7 +458,9 @@ def native(args, rank, world, device):
         "kernel_ms": kernel_ms, "kernel_launches": kernel_launches,
         "e2e_ms": sum(e2e_times), "e2e_nu": sum(s.node_updates for s in e2e_stats),
         "h2d": sum(s.h2d_bytes for s in e2e_stats) / len(e2e_stats),
-        "d2h": sum(s.d2h_bytes for s in e2e_stats) / len(e2e_stats) + host_out.numel() * 8,
+        "d2h": sum(s.d2h_bytes for s in e2e_stats) / len(e2e_stats),
+        "e2e_host_ms": {k: sum(getattr(s, k) for s in e2e_stats) / len(e2e_stats)
+                        for k in ("admit_ms", "rebuild_ms", "combine_ms")},
         "meshes": len(probs) * args.steps, "lat": lat, "wall_s": t_wall,
         "infos_steps": [i["steps"] for i in infos],
         "tuned": tuned, "window": opts["window_steps"],
@@ -506,13 +519,14 @@ def main():
                     help="c5: one Poisson rate (default: 0.25x..1.5x the saturation throughput)")
     ap.add_argument("--resident-steps", type=int, default=0,
                     help="steps a resident launch takes per window (0: the window's)")
-    ap.add_argument("--budget-mb", type=int, default=16,
+    ap.add_argument("--budget-mb", type=int, default=256,
                     help="c5: memory budget of the back-pressure run")
     ap.add_argument("--requests", type=int, default=64, help="c5: requests in the stream")
-    ap.add_argument("--plain-requests", type=int, default=16,
-                    help="c5: requests of the stream replayed on the plain FP64 path")
-    ap.add_argument("--max2d", type=int, default=513, help="c5: largest 2D side")
-    ap.add_argument("--max3d", type=int, default=65, help="c5: largest 3D side")
+    ap.add_argument("--plain-requests", type=int, default=-1,
+                    help="c5: requests of the stream replayed on the plain FP64 path "
+                         "(-1: the whole stream)")
+    ap.add_argument("--max2d", type=int, default=1025, help="c5: largest 2D side")
+    ap.add_argument("--max3d", type=int, default=193, help="c5: largest 3D side")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--max-steps", type=int, default=None,
                     help="override the per-request step cap (testing only)")
@@ -593,7 +607,10 @@ def main():
                                "step submitted together"},
         "mean_steps_per_request": float(np.mean(a0["infos_steps"])),
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": a0["h2d"],
-                "d2h_bytes_per_step": a0["d2h"]},
+                "d2h_bytes_per_step": a0["d2h"],
+                "path": "C ABI: pma_submit per request from host structs, pma_run, "
+                        "pma_get_mesh_batch into one page-locked host buffer",
+                "host_ms_per_step": a0["e2e_host_ms"]},
         "gpu_launches": a0["launches"] // max(args.steps, 1),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,

@@ -312,6 +312,19 @@ pma_status pma_get_mesh_device(pma_ctx *ctx, uint64_t req_id, void *x_dev, int32
 pma_status pma_get_mesh_device_batch(pma_ctx *ctx, int32_t n, const uint64_t *ids,
                                      void *const *x_dev, int32_t out_fp64);
 
+/* Batched pma_get_mesh into ONE caller-owned HOST buffer: the meshes of the
+ * n finished requests ids[0..n-1] are packed back to back in that order,
+ * request i's dim_i * N_i doubles (component-major) starting right after
+ * request i-1's.  One combination launch and one device-to-host copy for the
+ * whole batch (fastest into page-locked memory, e.g. cudaHostAlloc or
+ * cudaHostRegister; pageable memory works too).  infos (optional) receives n
+ * records.  Releases the requests.  Errors (nothing is released):
+ * PMA_ERR_NOT_FOUND (unknown id), PMA_ERR_BUSY (a request not finished or
+ * without a mesh), PMA_ERR_INVALID (NULL buffers, an id listed twice),
+ * PMA_ERR_CUDA.  Per-request outcomes are in infos[i].status.              */
+pma_status pma_get_mesh_batch(pma_ctx *ctx, int32_t n, const uint64_t *ids, double *x_out,
+                              pma_info *infos);
+
 /* FP64 positivity check of a finished request: recomputes det D_h^2 Psi in
  * FP64 at every global node (Sylvester minors of the symmetric FD Hessian)
  * and the signed measure of every mesh cell (2 triangles per quad in both
@@ -354,6 +367,9 @@ typedef struct {
   int64_t res_node_updates;
   double sweep_kernel_ms;         /* PMA_OPT_TIME_SWEEPS: device time of the sweeps */
   int64_t sweep_kernel_launches;  /* and the number of timed sweep launches        */
+  double admit_ms;                /* host wall time of admission passes            */
+  double rebuild_ms;              /* host wall time of table rebuilds              */
+  double combine_ms;              /* host wall time of pma_get_mesh_batch calls    */
 } pma_stats;
 pma_status pma_get_stats(pma_ctx *ctx, pma_stats *out, int32_t reset);
 

@@ -344,6 +344,8 @@ struct pma_ctx {
   // combine scratch
   CombineJob* d_jobs = nullptr;
   int jobs_cap = 0;
+  double* d_stage = nullptr;  // device staging of pma_get_mesh_batch
+  size_t stage_cap = 0;       // in doubles
   double* d_check = nullptr;
 
   // options
@@ -753,6 +755,7 @@ void fill_nb(const SubDesc* subs, int n, int dim, const int parts[3], int esize,
 // Rebuild subdomain table, work lists and problem descriptors for the
 // current active + finished requests.  Only active requests get tiles.
 pma_status rebuild(pma_ctx* c) {
+  const auto t_rb = Clock::now();
   c->h_subs.clear();
   c->h_nb.clear();
   c->h_tmap.clear();
@@ -858,6 +861,7 @@ pma_status rebuild(pma_ctx* c) {
   for (int k = 0; k < NUM_CLS; ++k) c->stats.h2d_bytes += (double)sizeof(WorkItem) * c->nwork[k];
   // The host-side vectors must stay alive until the copies complete.
   PMA_CK(cudaStreamSynchronize(c->stream));
+  c->stats.rebuild_ms += std::chrono::duration<double, std::milli>(Clock::now() - t_rb).count();
   c->dirty = false;
   c->graph_valid = false;
   c->res_dirty = true;
@@ -1214,6 +1218,8 @@ void collect(pma_ctx* c) {
 
 // Admit queued requests while memory and slots allow (lock held).
 pma_status admit(pma_ctx* c) {
+  const auto t0 = Clock::now();
+  bool admitted = false;
   while (!c->queue.empty()) {
     if (c->max_active > 0 && (int)c->active.size() >= c->max_active) break;
     Request& r = *c->reqs[c->queue.front()];
@@ -1245,19 +1251,25 @@ pma_status admit(pma_ctx* c) {
     r.slot = c->free_slots.back();
     c->free_slots.pop_back();
     r.res_class = pick_res_class(c, r, &r.res_smem);
-    ProbState ps{};
+    // the pinned mirror entry is the copy's source: it is not touched again
+    // before the synchronisation at the end of this admission pass
+    ProbState& ps = c->h_state[r.slot];
+    ps = ProbState{};
     ps.phase = PH_INIT_V;
     ps.status = PMA_PENDING;
     PMA_CK(cudaMemcpyAsync(c->d_state + r.slot, &ps, sizeof(ps), cudaMemcpyHostToDevice,
                            c->stream));
     c->stats.h2d_bytes += (double)sizeof(ps);
-    PMA_CK(cudaStreamSynchronize(c->stream));
-    c->h_state[r.slot] = ps;
+    admitted = true;
     r.state = RQ_ACTIVE;
     c->active.push_back(r.id);
     c->queue.pop_front();
     c->dirty = true;
   }
+  // tables, warm starts and initial states of every admitted request are in
+  // flight on the stream; their host sources must outlive the copies
+  if (admitted) PMA_CK(cudaStreamSynchronize(c->stream));
+  c->stats.admit_ms += std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
   return PMA_OK;
 }
 
@@ -1421,6 +1433,7 @@ pma_status pma_destroy(pma_ctx* c) {
     cudaFree(c->d_fin[k]);
   }
   cudaFree(c->d_jobs);
+  cudaFree(c->d_stage);
   cudaFree(c->d_check);
   cudaFree(c->d_queue);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -1823,6 +1836,68 @@ pma_status pma_get_mesh_device_batch(pma_ctx* c, int32_t n, const uint64_t* ids,
   PMA_CK(cudaStreamSynchronize(c->stream));
   c->stats.h2d_bytes += (double)sizeof(CombineJob) * jobs.size();
   c->stats.other_launches += 1;
+  return PMA_OK;
+}
+
+pma_status pma_get_mesh_batch(pma_ctx* c, int32_t n, const uint64_t* ids, double* x_out,
+                              pma_info* infos) {
+  if (!c || n < 0 || (n > 0 && (!ids || !x_out))) return PMA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (n == 0) return PMA_OK;
+  PMA_CK(cudaSetDevice(c->device));
+  const auto t0 = Clock::now();
+  std::vector<Request*> rs;
+  std::vector<size_t> off;
+  size_t total = 0;
+  long long blocks = 0;
+  for (int i = 0; i < n; ++i) {
+    auto it = c->reqs.find(ids[i]);
+    if (it == c->reqs.end()) return PMA_ERR_NOT_FOUND;
+    Request& r = *it->second;
+    if (r.state != RQ_FINISHED || !r.block) return PMA_ERR_BUSY;
+    for (Request* q : rs)
+      if (q == &r) {
+        set_err("pma_get_mesh_batch: request id listed twice");
+        return PMA_ERR_INVALID;
+      }
+    rs.push_back(&r);
+    off.push_back(total);
+    total += (size_t)r.dim * (size_t)r.nodes;
+  }
+  if (total > c->stage_cap) {
+    cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->stage_cap = 0;
+    PMA_CK(cudaMalloc(&c->d_stage, sizeof(double) * total));
+    c->stage_cap = total;
+  }
+  std::vector<CombineJob> jobs;
+  for (int i = 0; i < n; ++i) {
+    jobs.push_back(CombineJob{rs[i]->slot, 1, c->d_stage + off[i], nullptr, blocks});
+    blocks += (rs[i]->nodes + kCombineNodes - 1) / kCombineNodes;
+  }
+  if (c->dirty) {
+    pma_status st = rebuild(c);
+    if (st != PMA_OK) return st;
+  }
+  pma_status st = ensure_jobs(c, n);
+  if (st != PMA_OK) return st;
+  PMA_CK(cudaMemcpyAsync(c->d_jobs, jobs.data(), sizeof(CombineJob) * jobs.size(),
+                         cudaMemcpyHostToDevice, c->stream));
+  PMA_CK(launch_combine(c->d_jobs, n, blocks, c->d_subs, c->d_probs, c->d_state, c->stream));
+  PMA_CK(cudaMemcpyAsync(x_out, c->d_stage, sizeof(double) * total, cudaMemcpyDeviceToHost,
+                         c->stream));
+  PMA_CK(cudaStreamSynchronize(c->stream));
+  c->stats.h2d_bytes += (double)sizeof(CombineJob) * jobs.size();
+  c->stats.d2h_bytes += (double)sizeof(double) * total;
+  c->stats.other_launches += 1;
+  for (int i = 0; i < n; ++i) {
+    if (infos) infos[i] = rs[i]->info;
+    const uint64_t id = rs[i]->id;
+    free_request(c, *rs[i]);
+    c->reqs.erase(id);
+  }
+  c->stats.combine_ms += std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
   return PMA_OK;
 }
 

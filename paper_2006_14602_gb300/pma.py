@@ -104,7 +104,9 @@ class pma_stats(C.Structure):
                 ("sweep_bytes", C.c_double), ("window_ms", C.c_double),
                 ("h2d_bytes", C.c_double), ("d2h_bytes", C.c_double),
                 ("res_launches", C.c_int64), ("res_node_updates", C.c_int64),
-                ("sweep_kernel_ms", C.c_double), ("sweep_kernel_launches", C.c_int64)]
+                ("sweep_kernel_ms", C.c_double), ("sweep_kernel_launches", C.c_int64),
+                ("admit_ms", C.c_double), ("rebuild_ms", C.c_double),
+                ("combine_ms", C.c_double)]
 
 
 _lib = None
@@ -129,6 +131,8 @@ _SIGS = {
     "pma_admit": (C.c_int, [C.c_void_p]),
     "pma_get_mesh_device_batch": (C.c_int, [C.c_void_p, C.c_int32, _P(C.c_uint64),
                                             _P(C.c_void_p), C.c_int32]),
+    "pma_get_mesh_batch": (C.c_int, [C.c_void_p, C.c_int32, _P(C.c_uint64), _P(C.c_double),
+                                     _P(pma_info)]),
     "pma_get_stats": (C.c_int, [C.c_void_p, _P(pma_stats), C.c_int32]),
     "pma_poll": (C.c_int, [C.c_void_p, C.c_uint64, _P(C.c_int32)]),
     "pma_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64]),
@@ -251,6 +255,16 @@ def pma_get_mesh_device_batch(ctx, ids: Sequence[int], x_dev_ptrs: Sequence[int]
     a = (C.c_uint64 * max(n, 1))(*ids)
     b = (C.c_void_p * max(n, 1))(*[C.c_void_p(p) for p in x_dev_ptrs])
     return _call("pma_get_mesh_device_batch", ctx, n, a, b, out_fp64)
+
+
+def pma_get_mesh_batch(ctx, ids: Sequence[int], x_out_ptr: int, infos=None) -> int:
+    """Meshes of finished requests packed back to back into one host buffer
+    at address x_out_ptr (doubles); infos: optional ctypes array of pma_info
+    with len(ids) entries."""
+    n = len(ids)
+    a = (C.c_uint64 * max(n, 1))(*ids)
+    return _call("pma_get_mesh_batch", ctx, n, a, C.cast(C.c_void_p(x_out_ptr), _P(C.c_double)),
+                 infos)
 
 
 def pma_get_stats(ctx, reset: int = 0):

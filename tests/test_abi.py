@@ -46,13 +46,14 @@ _LAYOUT_PROBE = r"""
 #define F(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
 int main(void) {
   printf("pma_grid %zu\npma_term %zu\npma_monitor %zu\npma_decomp %zu\n"
-         "pma_params %zu\npma_info %zu\n", sizeof(pma_grid), sizeof(pma_term),
-         sizeof(pma_monitor), sizeof(pma_decomp), sizeof(pma_params), sizeof(pma_info));
+         "pma_params %zu\npma_info %zu\npma_stats %zu\n", sizeof(pma_grid), sizeof(pma_term),
+         sizeof(pma_monitor), sizeof(pma_decomp), sizeof(pma_params), sizeof(pma_info),
+         sizeof(pma_stats));
   F(pma_grid, lo) F(pma_grid, hi) F(pma_term, amp) F(pma_term, c)
   F(pma_monitor, base) F(pma_monitor, term) F(pma_decomp, overlap)
   F(pma_decomp, exchange_every)
   F(pma_params, max_steps) F(pma_params, precision) F(pma_info, status)
-  F(pma_info, latency_us)
+  F(pma_info, latency_us) F(pma_stats, sweep_kernel_launches) F(pma_stats, combine_ms)
   return 0;
 }
 """
@@ -67,7 +68,8 @@ def test_struct_layout_matches_header():
         lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
     got = dict(l.split() for l in lines.strip().splitlines())
     S = {"pma_grid": pma.pma_grid, "pma_term": pma.pma_term, "pma_monitor": pma.pma_monitor,
-         "pma_decomp": pma.pma_decomp, "pma_params": pma.pma_params, "pma_info": pma.pma_info}
+         "pma_decomp": pma.pma_decomp, "pma_params": pma.pma_params, "pma_info": pma.pma_info,
+         "pma_stats": pma.pma_stats}
     for k, v in got.items():
         if "." in k:
             s, f = k.split(".")
