@@ -317,6 +317,9 @@ struct pma_ctx {
   std::vector<CUtensorMap> h_tmap;
   unsigned int h_err = 0;
   std::vector<WorkItem> h_work[NUM_CLS];
+  std::vector<int> h_order[NUM_CLS];  // largest-first order of the work list
+  int* d_order[NUM_CLS] = {};
+  size_t order_cap[NUM_CLS] = {};
   bool dirty = true;
   long long dead_tiles = 0, live_tiles = 0;
 
@@ -845,6 +848,23 @@ pma_status rebuild(pma_ctx* c) {
       PMA_CK(cudaMemcpyAsync(c->d_work[k], c->h_work[k].data(),
                              sizeof(WorkItem) * c->nwork[k], cudaMemcpyHostToDevice,
                              c->stream));
+    // largest items first (ties in list order): the persistent CTAs then
+    // end the launch on the smallest items instead of a few large ones
+    std::vector<int>& ord = c->h_order[k];
+    ord.resize(c->nwork[k]);
+    for (int t = 0; t < c->nwork[k]; ++t) ord[t] = t;
+    const std::vector<WorkItem>& wl = c->h_work[k];
+    auto size_of = [&](int t) {
+      const WorkItem& w = wl[t];
+      const long long d = (k == CLS_3D_F32 || k == CLS_3D_F64) ? (w.kz >> 16) : 1;
+      return (long long)(w.ext & 0xffff) * (long long)(w.ext >> 16) * d;
+    };
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int x, int y) { return size_of(x) > size_of(y); });
+    if ((st = ensure_buf(&c->d_order[k], &c->order_cap[k], ord.size() + 1)) != PMA_OK) return st;
+    if (c->nwork[k])
+      PMA_CK(cudaMemcpyAsync(c->d_order[k], ord.data(), sizeof(int) * ord.size(),
+                             cudaMemcpyHostToDevice, c->stream));
     const int per_sm = sweep_max_blocks_per_sm(k, c->tile_id[k]);
     c->grid[k] = std::min(c->nwork[k], per_sm * c->num_sms);
   }
@@ -1015,6 +1035,11 @@ LaunchArgs args_for(pma_ctx* c, int k, int t0, int n) {
   a.part = c->d_part[k];
   a.queue = c->d_queue + 2 * k;
   a.grid = std::min(n, c->grid[k] > 0 ? c->grid[k] : n);
+  // the whole class list in one launch takes the largest items first; the
+  // per-subdomain launches of the plain path take theirs in list order
+  a.order = (t0 == 0 && n == c->nwork[k] && c->launch_mode == PMA_LAUNCH_BATCHED)
+                ? c->d_order[k]
+                : nullptr;
   return a;
 }
 
@@ -1429,6 +1454,7 @@ pma_status pma_destroy(pma_ctx* c) {
   cudaFree(c->d_tmap);
   for (int k = 0; k < NUM_CLS; ++k) {
     cudaFree(c->d_work[k]);
+    cudaFree(c->d_order[k]);
     cudaFree(c->d_part[k]);
     cudaFree(c->d_fin[k]);
   }
@@ -2102,6 +2128,7 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   la.st = (ProbState*)(B + o_st);
   la.part = (Partial*)(B + o_part);
   la.queue = (unsigned int*)(B + o_q) + 2 * cls;
+  la.order = nullptr;
   la.grid = std::min(la.nwork, sweep_max_blocks_per_sm(cls, 0) * num_sms);
 
   // step in windows until the request is done (two extra launches cover

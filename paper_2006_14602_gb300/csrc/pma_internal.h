@@ -256,6 +256,11 @@ struct LaunchArgs {
   Partial* part;
   unsigned int* queue;   // two counters: next work item, CTAs finished
   int grid;              // CTAs (persistent, pulling work items)
+  // Order in which the persistent CTAs take the work items (a permutation
+  // of [0, nwork): largest items first, so that the launch ends on small
+  // ones), or null for list order.  Records stay indexed by the item, so the
+  // order changes no result.
+  const int* order;
 };
 
 int tile2d_count();

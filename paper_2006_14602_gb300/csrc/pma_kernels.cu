@@ -475,12 +475,15 @@ __device__ __forceinline__ TrBox3 tr_box3(int dlx, int dhx, int dly, int dhy, in
 }
 
 // ---------------------------------------------------------------- work queue
-// Persistent CTAs pull work items from a per-launch counter; the last CTA
-// to run out resets the counters for the next launch.  The partial record
+// Persistent CTAs pull work items from a per-launch counter (through the
+// launch's order table when it has one); the last CTA to run out resets the
+// counters for the next launch.  The partial record
 // of an item is indexed by the item, so results do not depend on which CTA
 // took it.
 __device__ __forceinline__ int pull_item(const LaunchArgs& a) {
-  return a.t0 + (int)atomicAdd(a.queue, 1u);
+  const int q = (int)atomicAdd(a.queue, 1u);
+  if (a.order == nullptr || q >= a.nwork) return a.t0 + q;
+  return a.t0 + __ldg(a.order + q);
 }
 __device__ __forceinline__ void queue_exit(const LaunchArgs& a) {
   __threadfence();
