@@ -882,8 +882,8 @@ __device__ __forceinline__ void issue_hdr(const LaunchArgs& a, BandHdr<T>& H, co
 // and writes the 4 results with one 16-byte store.  Shared row layout: node
 // column c sits at c + 4 (halo columns at 3 and cols + 4), rows are `SWp`
 // (a multiple of 4) wide.
-template <typename T, int NT, int SMAX>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 896 : 512) / NT) k_band2d(LaunchArgs a) {
+template <typename T, int NT, int SMAX, int MB>
+__global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
   // programmatic dependent launch: wait until the preceding kernel of the
   // stream has completed and its writes are visible
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -2156,19 +2156,22 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
 
 // ---------------------------------------------------------------- dispatch
 // Compiled shapes.  2D: (threads, band nodes FP32, band nodes FP64, shared
-// elements per band node x 10): the staged band plus halo and the column
+// elements per band node x 10, FP32 CTAs per SM the registers are budgeted
+// for; FP64 budgets for 4): the staged band plus halo and the column
 // tables fit in nodes x factor / 10 elements (bands get fewer rows, or
 // narrower strips, where the halo would not fit).
-#define PMA_T2D(X) X(128, 3072, 1536, 16) X(128, 2048, 1024, 30) X(128, 4096, 2048, 14) \
-                   X(128, 5120, 2560, 14) X(128, 768, 384, 30)
+#define PMA_T2D(X) X(128, 3072, 1536, 16, 7) X(128, 2048, 1024, 30, 7) \
+                   X(128, 4096, 2048, 14, 7) X(128, 5120, 2560, 14, 7) \
+                   X(128, 768, 384, 30, 7) X(128, 6144, 3072, 14, 6) X(128, 4096, 2048, 14, 6)
 #define PMA_SMAX(n, f) (((n) * (f) / 10) & ~3)
 // 3D: (threads, nodes per plane box, planes FP32, planes FP64, dynamic
 // shared memory in KiB for the staged box and the column tables, FP32 CTAs
 // per SM the registers are budgeted for; FP64 budgets for 2).
-#define PMA_T3D(X) X(128, 512, 8, 4, 32, 3) X(128, 512, 8, 4, 32, 4) X(128, 512, 8, 4, 64, 3)
+#define PMA_T3D(X) X(128, 512, 8, 4, 32, 3) X(128, 512, 8, 4, 32, 4) X(128, 512, 8, 4, 64, 3) \
+                   X(128, 512, 8, 4, 32, 5) X(128, 512, 8, 4, 32, 6)
 
 static const int k_t2d[][4] = {
-#define E(a, b, c, f) {a, b, c, f},
+#define E(a, b, c, f, m) {a, b, c, f},
     PMA_T2D(E)
 #undef E
 };
@@ -2208,13 +2211,13 @@ static const void* sweep_fn(int dim, int id, int* nthreads, int* dyn) {
   int k = 0;
   *dyn = 0;
   if (dim == 2) {
-#define E(a, b, c, f)                                                      \
+#define E(a, b, c, f, m)                                                   \
   if (k++ == id) {                                                         \
     *nthreads = (a);                                                       \
     if constexpr (sizeof(T) == 8)                                          \
-      return (const void*)k_band2d<T, a, PMA_SMAX(c, f)>;                  \
+      return (const void*)k_band2d<T, a, PMA_SMAX(c, f), 512 / (a)>;       \
     else                                                                   \
-      return (const void*)k_band2d<T, a, PMA_SMAX(b, f)>;                  \
+      return (const void*)k_band2d<T, a, PMA_SMAX(b, f), m>;               \
   }
     PMA_T2D(E)
 #undef E
