@@ -154,6 +154,79 @@ def serving(args):
     return 0
 
 
+# ------------------------------------------------------------------ per-config table
+def config_table(args):
+    """Configurations 1-4 on three device paths (FP32 batched, FP64 batched,
+    the plain FP64 path: one launch per subdomain and step, no graphs) and
+    the FP64 oracle on one host core (a bounded sample of each
+    configuration, step caps scaled to ~1.5e8 node-updates).  Device time
+    from CUDA events around pma_run on the context's stream; L2 flushed
+    before each timed run.  One JSON line."""
+    import torch
+    from paper_2006_14602_gb300 import build, pma
+
+    cfgs = {"c1": [W.config1("fp64")],
+            "c2": [W.config2("ring", "fp64"), W.config2("sine", "fp64")],
+            "c3": [W.config3("fp64")],
+            "c4": W.config4(precision="fp64")}
+    # oracle first, in spawned workers of one process each, before any GPU call
+    oracle_rates = {}
+    for name, probs in cfgs.items():
+        work = sum(_sub_nodes(p) * p.max_steps for p in probs)
+        scale = min(1.0, 1.5e8 / work)
+        rng = np.random.default_rng(3)
+        pick = probs if len(probs) <= 2 else [probs[i] for i in rng.permutation(len(probs))[:8]]
+        sample = [p.replace(max_steps=max(1, int(p.max_steps * scale)), tol=0.0) for p in pick]
+        v, wall, nu = run_oracle(sample, 1)
+        oracle_rates[name] = {"node_updates_per_s": v, "sample_node_updates": nu, "wall_s": wall,
+                              "cores": 1}
+    build.build()
+    pma.load()
+    torch.cuda.init()
+    stream = torch.cuda.Stream(0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=0)
+
+    def timed(probs, precision, plain):
+        opts = {"window_steps": 128}
+        if plain:
+            opts.update(launch_mode=pma.PMA_LAUNCH_PER_SUBDOMAIN, use_graphs=0)
+        ps = [p.replace(precision=precision) for p in probs]
+        with pma.Context(0, 0, stream.cuda_stream, **opts) as ctx:
+            for _ in range(2):  # the first pass warms up
+                ids = [ctx.submit(p) for p in ps]
+                if pma.pma_admit(ctx.h) != pma.PMA_OK:
+                    raise RuntimeError("admission failed")
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                pma.pma_get_stats(ctx.h, 1)
+                e0.record(stream)
+                ctx.run()
+                e1.record(stream)
+                e1.synchronize()
+                _, st = pma.pma_get_stats(ctx.h, 1)
+                steps = []
+                for i in ids:
+                    steps.append(pma.pma_get_info(ctx.h, i)[1].steps)
+                    pma.pma_release(ctx.h, i)
+            ms = e0.elapsed_time(e1)
+        return {"node_updates_per_s": st.node_updates / (ms / 1e3), "meshes_per_s":
+                len(ps) / (ms / 1e3), "ms": ms, "mean_steps": float(np.mean(steps))}
+
+    table = {}
+    for name, probs in cfgs.items():
+        table[name] = {"oracle_1_core": oracle_rates[name],
+                       "gpu_fp32_batched": timed(probs, "fp32", False),
+                       "gpu_fp64_batched": timed(probs, "fp64", False),
+                       "gpu_fp64_plain": timed(probs, "fp64", True)}
+    line = {"metric": "per-configuration node-updates/s (configs 1-4)", "unit": "node-updates/s",
+            "n_gpus": 1, "data": "synthetic (seeded requests, master seed %d)" % W.MASTER_SEED,
+            "configs": table}
+    print(json.dumps(line))
+    return 0
+
+
 def make_workload(name: str, precision: str, max_steps=None):
     if name == "c4":
         probs = W.config4(precision=precision)
@@ -351,12 +424,13 @@ def native(args, rank, world, device):
     stream = torch.cuda.Stream(device)
     probs = make_workload(args.workload, args.precision, args.max_steps)
     # one step in 16 of every window has its sweep launch timed with events
-    opts = {"window_steps": args.window, "resident": args.resident, "time_sweeps": 16}
+    opts = {"window_steps": args.window, "resident": args.resident, "time_sweeps": 16,
+            "groups": args.groups}
     tuned = None
     if args.autotune and args.tile2d is None and args.tile3d is None and not args.resident:
         # untimed: work shapes and window length measured on this batch
         from paper_2006_14602_gb300.autotune import autotune
-        tuned = autotune(probs, device)
+        tuned = autotune(probs, device, groups=args.groups)
         opts.update(tile_2d=tuned["tile_2d"], tile_3d=tuned["tile_3d"],
                     window_steps=tuned["window_steps"])
     if args.tile2d is not None:
@@ -451,10 +525,12 @@ def native(args, rank, world, device):
     kernel_ms = sum(s.sweep_kernel_ms for s in all_stats)
     kernel_launches = sum(s.sweep_kernel_launches for s in all_stats)
     launches = sum(s.sweep_launches for s in all_stats)
+    sweep_steps = sum(s.sweep_steps for s in all_stats)
     other = sum(s.other_launches for s in all_stats)
     local = {
         "node_updates": node_updates, "ms": total_ms, "sweep_ms": sweep_ms,
         "sweep_bytes": sweep_bytes, "launches": launches + other, "sweep_launches": launches,
+        "sweep_steps": sweep_steps,
         "kernel_ms": kernel_ms, "kernel_launches": kernel_launches,
         "e2e_ms": sum(e2e_times), "e2e_nu": sum(s.node_updates for s in e2e_stats),
         "h2d": sum(s.h2d_bytes for s in e2e_stats) / len(e2e_stats),
@@ -511,7 +587,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS) + ["c5"])
+    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS) + ["c5", "table"])
     ap.add_argument("--resident", type=int, default=0,
                     help="k > 0: cluster-resident path for 2D requests that fit the "
                          "first k shared-memory classes (0: band kernels only)")
@@ -531,6 +607,8 @@ def main():
     ap.add_argument("--max-steps", type=int, default=None,
                     help="override the per-request step cap (testing only)")
     ap.add_argument("--window", type=int, default=64)
+    ap.add_argument("--groups", type=int, default=1,
+                    help="request groups per kernel class (1 or 2), each on its own stream")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip the untimed autotuning of work shapes and window length")
     ap.add_argument("--tile2d", type=int, default=None, help="2D work shape id (default: auto)")
@@ -548,6 +626,8 @@ def main():
         return reference_arm(args, world)
     if args.workload == "c5":
         return serving(args) if rank == 0 else 0
+    if args.workload == "table":
+        return config_table(args) if rank == 0 else 0
 
     if world > 1:
         import torch
@@ -575,11 +655,14 @@ def main():
     # the sweep kernel's own device time: CUDA events around every sweep launch
     # on the library's stream (recorded inside the windows' graphs)
     if a0["kernel_ms"] > 0 and not args.resident:
-        achieved = a0["sweep_bytes"] / (a0["kernel_ms"] / 1e3) / 1e9
-        timing = ("CUDA events around the sweep launch of one step in 16 of the timed "
-                  "region (%d launches timed, mean %.1f us)" % (
-                      a0["kernel_launches"], 1e3 * a0["kernel_ms"] / max(a0["kernel_launches"], 1)))
-        per_launch = a0["sweep_bytes"] / max(a0["sweep_launches"], 1)
+        timing = ("CUDA events around the sweep launches of one step in 16 of the timed "
+                  "region, on the launching streams: %d steps timed, mean %.1f us from the "
+                  "first group's sweep start to the last one's end (request groups: %d, "
+                  "their sweeps overlap)" % (
+                      a0["kernel_launches"], 1e3 * a0["kernel_ms"] / max(a0["kernel_launches"], 1),
+                      args.groups))
+        # algorithmic bytes of one step's sweep launches over their timed span
+        per_launch = a0["sweep_bytes"] / max(a0["sweep_steps"], 1)
         achieved = per_launch / (a0["kernel_ms"] / max(a0["kernel_launches"], 1) / 1e3) / 1e9
     else:
         achieved = a0["sweep_bytes"] / (a0["sweep_ms"] / 1e3) / 1e9
@@ -598,7 +681,7 @@ def main():
                    "precision": args.precision, "window_steps": a0["window"],
                    "autotuned": ({k: v for k, v in a0["tuned"].items() if k != "rates"}
                                  if a0["tuned"] else None),
-                   "resident": args.resident,
+                   "resident": args.resident, "request_groups": args.groups,
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "meshes_per_s": a0["meshes"] / (a0["ms"] / 1e3),
@@ -620,6 +703,7 @@ def main():
                      "algorithmic_bytes_per_node_update": 2 * (4 if args.precision == "fp32" else 8)},
         "cpu_baseline": cpu,
         "clocks": clocks,
+        "autotune_rates": a0["tuned"]["rates"] if a0["tuned"] else None,
     }
     print(json.dumps(line))
     return 0

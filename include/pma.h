@@ -227,11 +227,14 @@ pma_status pma_destroy(pma_ctx *ctx);
  *                          kernels only (default).  Batched launch mode only;
  *                          decided per request when it is admitted.
  *   PMA_OPT_TIME_SWEEPS    k > 0: time the sweep launches of every k-th step
- *                          of a window with a pair of CUDA events on the
- *                          context's stream (recorded inside the windows'
- *                          graphs; each pair costs about a microsecond, so
- *                          k = 1 slows a step by several per cent); sums in
- *                          pma_stats (sweep_kernel_ms, sweep_kernel_launches).
+ *                          of a window with CUDA events, a pair around each
+ *                          group's sweep on the group's stream (recorded
+ *                          inside the windows' graphs; each pair costs about a
+ *                          microsecond, so k = 1 slows a step by several per
+ *                          cent); a timed (step, class) counts from its first
+ *                          sweep's start to its last sweep's end (the groups'
+ *                          sweeps overlap); sums in pma_stats
+ *                          (sweep_kernel_ms, sweep_kernel_launches).
  *                          0 = off (default).
  *   PMA_OPT_RESIDENT_STEPS steps a resident launch takes per window (0 = the
  *                          window's steps, default).  A resident step costs
@@ -247,11 +250,20 @@ pma_status pma_destroy(pma_ctx *ctx);
  *                          the step's finish pass retires every active request
  *                          with PMA_ERR_TIMEOUT (later sweeps skip their work)
  *                          and pma_run returns PMA_ERR_TIMEOUT; the context
- *                          stays usable.  0 = off (default). */
+ *                          stays usable.  0 = off (default).
+ *   PMA_OPT_GROUPS         request groups per kernel class in the batched
+ *                          mode, 1 (default) or 2: the admitted requests of
+ *                          a class are split into groups of about equal node
+ *                          count, and each group's sweep and finish launches
+ *                          run on their own stream (captured in the same
+ *                          graph), so that one group's finish pass and launch
+ *                          tail overlap the other's sweep.  Requests are
+ *                          independent, so results do not depend on it
+ *                          (bitwise). */
 enum { PMA_OPT_WINDOW_STEPS = 1, PMA_OPT_USE_GRAPHS = 2, PMA_OPT_LAUNCH_MODE = 3,
        PMA_OPT_TILE_2D = 4, PMA_OPT_TILE_3D = 5, PMA_OPT_MAX_ACTIVE = 6,
        PMA_OPT_RESIDENT = 7, PMA_OPT_TIME_SWEEPS = 8, PMA_OPT_RESIDENT_STEPS = 9,
-       PMA_OPT_TEST_STALL = 10 };
+       PMA_OPT_TEST_STALL = 10, PMA_OPT_GROUPS = 11 };
 enum { PMA_LAUNCH_BATCHED = 0, PMA_LAUNCH_PER_SUBDOMAIN = 1 };
 pma_status pma_set_option(pma_ctx *ctx, int32_t option, int64_t value);
 pma_status pma_get_option(pma_ctx *ctx, int32_t option, int64_t *value);
@@ -365,11 +377,14 @@ typedef struct {
   double d2h_bytes;
   int64_t res_launches;
   int64_t res_node_updates;
-  double sweep_kernel_ms;         /* PMA_OPT_TIME_SWEEPS: device time of the sweeps */
-  int64_t sweep_kernel_launches;  /* and the number of timed sweep launches        */
+  double sweep_kernel_ms;         /* PMA_OPT_TIME_SWEEPS: device time of the sweeps
+                                     of the timed (step, class) pairs            */
+  int64_t sweep_kernel_launches;  /* and the number of timed (step, class) pairs   */
   double admit_ms;                /* host wall time of admission passes            */
   double rebuild_ms;              /* host wall time of table rebuilds              */
   double combine_ms;              /* host wall time of pma_get_mesh_batch calls    */
+  int64_t sweep_steps;            /* (step, kernel class) pairs the band sweeps ran;
+                                     sweep_bytes / sweep_steps = bytes per step   */
 } pma_stats;
 pma_status pma_get_stats(pma_ctx *ctx, pma_stats *out, int32_t reset);
 

@@ -79,6 +79,7 @@ struct Request {
   int slot = -1;
   int res_class = -1;        // resident class, -1: band kernel (fixed at admission)
   int res_smem = 0;          // shared memory one resident CTA of it needs (max over subs)
+  int group = 0;             // request group of its class (set by each rebuild)
   ReqState state = RQ_QUEUED;
   pma_info info{};
   Clock::time_point t_submit, t_done;
@@ -268,6 +269,11 @@ pma_status build_request(Request& r) {
 }  // namespace
 
 // ============================================================== context
+// Request groups per class (see pma_ctx::ngroups) and the position of the
+// device error word after the groups' queue counters.
+constexpr int kGroups = 2;
+constexpr int kErrWord = 2 * NUM_CLS * kGroups;
+
 struct pma_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -305,21 +311,33 @@ struct pma_ctx {
   Partial* d_part[NUM_CLS] = {};
   size_t work_cap[NUM_CLS] = {};
   int nwork[NUM_CLS] = {};
-  int* d_fin[NUM_CLS] = {};           // live problem slots per class
-  size_t fin_cap[NUM_CLS] = {};
-  int nfin[NUM_CLS] = {};
-  std::vector<int> h_fin[NUM_CLS];
-  unsigned int* d_queue = nullptr;  // 2 counters per class, then the error word
-  int grid[NUM_CLS] = {};
+  // Request groups: the live requests of a class are split into kGroups
+  // groups of about equal node count; each group's items are a contiguous
+  // range of the class work list and run as their own sweep + finish chain
+  // on their own stream, so that one group's finish pass and launch tail
+  // overlap the other group's sweep.  Index kg = k * kGroups + g.
+  int ngroups = 1;                        // PMA_OPT_GROUPS (1 or kGroups)
+  int gbeg[NUM_CLS * kGroups] = {};       // first item of the group
+  int gcnt[NUM_CLS * kGroups] = {};       // items of the group
+  int* d_fin[NUM_CLS * kGroups] = {};     // live problem slots per group
+  size_t fin_cap[NUM_CLS * kGroups] = {};
+  int nfin[NUM_CLS * kGroups] = {};
+  std::vector<int> h_fin[NUM_CLS * kGroups];
+  // 2 counters per class and group, then the error word (kErrWord)
+  unsigned int* d_queue = nullptr;
+  int grid[NUM_CLS * kGroups] = {};
+  cudaStream_t gstream[kGroups] = {};     // [0] = the context's stream
+  cudaEvent_t ev_gfork = nullptr, ev_gjoin[kGroups] = {};
   int tile_id[NUM_CLS] = {};
   std::vector<SubDesc> h_subs;
   std::vector<NbEnt> h_nb;
   std::vector<CUtensorMap> h_tmap;
   unsigned int h_err = 0;
   std::vector<WorkItem> h_work[NUM_CLS];
-  std::vector<int> h_order[NUM_CLS];  // largest-first order of the work list
-  int* d_order[NUM_CLS] = {};
-  size_t order_cap[NUM_CLS] = {};
+  // largest-first order of each group's items (relative to the group start)
+  std::vector<int> h_order[NUM_CLS * kGroups];
+  int* d_order[NUM_CLS * kGroups] = {};
+  size_t order_cap[NUM_CLS * kGroups] = {};
   bool dirty = true;
   long long dead_tiles = 0, live_tiles = 0;
 
@@ -370,6 +388,7 @@ struct pma_ctx {
   int opt_test_stall = 0;  // test hook of the bounded TMA wait
   bool time_this_step = false;
   std::vector<cudaEvent_t> tev;
+  std::vector<int> tev_groups;  // per timed (step, class): groups, 2 events each
   int tev_used = 0;
   bool capturing = false;
   int graph_steps_timed = 0;
@@ -762,60 +781,98 @@ pma_status rebuild(pma_ctx* c) {
   c->h_subs.clear();
   c->h_nb.clear();
   c->h_tmap.clear();
+  const int G = (c->launch_mode == PMA_LAUNCH_BATCHED) ? std::max(1, std::min(c->ngroups, kGroups)) : 1;
   for (int k = 0; k < NUM_CLS; ++k) {
     c->h_work[k].clear();
-    c->h_fin[k].clear();
+    for (int g = 0; g < kGroups; ++g) c->h_fin[k * kGroups + g].clear();
     c->tile_id[k] = pick_tile(c, k);
   }
   c->live_tiles = 0;
   c->dead_tiles = 0;
-  for (auto& kv : c->reqs) {
-    Request& r = *kv.second;
-    if (r.state == RQ_QUEUED || r.slot < 0) continue;
-    ProbDesc& pd = c->h_probs[r.slot];
-    fill_probdesc(r, pd);
-    pd.sub_base = (int)c->h_subs.size();
-    std::vector<WorkItem>& wl = c->h_work[r.cls];
-    // resident requests take no band tiles and no finish pass
-    const bool live = (r.state == RQ_ACTIVE) && r.res_class < 0;
-    pd.tile_begin = (int)wl.size();
-    for (size_t si = 0; si < r.subs.size(); ++si) {
-      const HostSub& hs = r.subs[si];
-      SubDesc sd{};
-      sd.prob = r.slot;
-      for (int a = 0; a < 3; ++a) {
-        sd.n[a] = hs.n[a];
-        sd.g0[a] = hs.g0[a];
-        sd.clo[a] = hs.clo[a];
-        sd.chi[a] = hs.chi[a];
-        sd.k[a] = hs.k[a];
+  // groups: per class, the live band requests in decreasing subdomain-node
+  // count, each to the group with the fewest nodes so far (ties: lower group)
+  auto is_live = [](const Request& r) {
+    return r.state == RQ_ACTIVE && r.slot >= 0 && r.res_class < 0;
+  };
+  {
+    std::vector<Request*> byc[NUM_CLS];
+    for (auto& kv : c->reqs)
+      if (is_live(*kv.second)) byc[kv.second->cls].push_back(kv.second.get());
+    for (int k = 0; k < NUM_CLS; ++k) {
+      std::stable_sort(byc[k].begin(), byc[k].end(), [](const Request* a, const Request* b) {
+        return a->sub_nodes > b->sub_nodes;
+      });
+      long long load[kGroups] = {};
+      for (Request* r : byc[k]) {
+        int g = 0;
+        for (int q = 1; q < G; ++q)
+          if (load[q] < load[g]) g = q;
+        r->group = g;
+        load[g] += r->sub_nodes;
       }
-      sd.faces = hs.faces;
-      sd.idx = hs.idx;
-      sd.pitch = hs.pitch;
-      sd.v[0] = r.block + hs.off[0];
-      sd.v[1] = r.block + hs.off[1];
-      sd.tile_begin = (int)wl.size();
-      if (live)
-        push_items(hs, r.dim, r.esize == 8, c->tile_id[r.cls], (int)c->h_subs.size(), r.slot, wl);
-      sd.tile_end = (int)wl.size();
-      assign_maps(sd, r.dim, r.esize, hs.n[0], wl.data() + sd.tile_begin,
-                  sd.tile_end - sd.tile_begin, c->h_tmap);
-      c->h_subs.push_back(sd);
     }
-    pd.tile_end = (int)wl.size();
-    const int nb_base = (int)c->h_nb.size();
-    fill_nb(c->h_subs.data() + pd.sub_base, (int)r.subs.size(), r.dim, pd.parts, r.esize,
-            c->h_nb);
-    if (live) {
-      c->live_tiles += pd.tile_end - pd.tile_begin;
-      c->h_fin[r.cls].push_back(r.slot);
-    }
-    fill_hot<float>(r, pd, c->h_hotf[r.slot]);
-    fill_hot<double>(r, pd, c->h_hotd[r.slot]);
-    c->h_hotf[r.slot].nb_base = nb_base;
-    c->h_hotd[r.slot].nb_base = nb_base;
   }
+  // pass g emits the requests of group g (pass 0 also those without band
+  // items: finished, or on the resident path), so every group's items are
+  // one contiguous range of its class list
+  for (int g = 0; g < G; ++g) {
+    for (int k = 0; k < NUM_CLS; ++k) c->gbeg[k * kGroups + g] = (int)c->h_work[k].size();
+    for (auto& kv : c->reqs) {
+      Request& r = *kv.second;
+      if (r.state == RQ_QUEUED || r.slot < 0) continue;
+      const bool live = is_live(r);
+      if (live ? r.group != g : g != 0) continue;
+      ProbDesc& pd = c->h_probs[r.slot];
+      fill_probdesc(r, pd);
+      pd.sub_base = (int)c->h_subs.size();
+      std::vector<WorkItem>& wl = c->h_work[r.cls];
+      pd.tile_begin = (int)wl.size();
+      for (size_t si = 0; si < r.subs.size(); ++si) {
+        const HostSub& hs = r.subs[si];
+        SubDesc sd{};
+        sd.prob = r.slot;
+        for (int a = 0; a < 3; ++a) {
+          sd.n[a] = hs.n[a];
+          sd.g0[a] = hs.g0[a];
+          sd.clo[a] = hs.clo[a];
+          sd.chi[a] = hs.chi[a];
+          sd.k[a] = hs.k[a];
+        }
+        sd.faces = hs.faces;
+        sd.idx = hs.idx;
+        sd.pitch = hs.pitch;
+        sd.v[0] = r.block + hs.off[0];
+        sd.v[1] = r.block + hs.off[1];
+        sd.tile_begin = (int)wl.size();
+        if (live)
+          push_items(hs, r.dim, r.esize == 8, c->tile_id[r.cls], (int)c->h_subs.size(), r.slot,
+                     wl);
+        sd.tile_end = (int)wl.size();
+        assign_maps(sd, r.dim, r.esize, hs.n[0], wl.data() + sd.tile_begin,
+                    sd.tile_end - sd.tile_begin, c->h_tmap);
+        c->h_subs.push_back(sd);
+      }
+      pd.tile_end = (int)wl.size();
+      const int nb_base = (int)c->h_nb.size();
+      fill_nb(c->h_subs.data() + pd.sub_base, (int)r.subs.size(), r.dim, pd.parts, r.esize,
+              c->h_nb);
+      if (live) {
+        c->live_tiles += pd.tile_end - pd.tile_begin;
+        c->h_fin[r.cls * kGroups + g].push_back(r.slot);
+      }
+      fill_hot<float>(r, pd, c->h_hotf[r.slot]);
+      fill_hot<double>(r, pd, c->h_hotd[r.slot]);
+      c->h_hotf[r.slot].nb_base = nb_base;
+      c->h_hotd[r.slot].nb_base = nb_base;
+    }
+    for (int k = 0; k < NUM_CLS; ++k)
+      c->gcnt[k * kGroups + g] = (int)c->h_work[k].size() - c->gbeg[k * kGroups + g];
+  }
+  for (int k = 0; k < NUM_CLS; ++k)
+    for (int g = G; g < kGroups; ++g) {
+      c->gbeg[k * kGroups + g] = (int)c->h_work[k].size();
+      c->gcnt[k * kGroups + g] = 0;
+    }
   pma_status st;
   if ((st = ensure_buf(&c->d_subs, &c->subs_cap, c->h_subs.size() + 1)) != PMA_OK) return st;
   if ((st = ensure_buf(&c->d_nb, &c->nb_cap, c->h_nb.size() + 1)) != PMA_OK) return st;
@@ -838,35 +895,41 @@ pma_status rebuild(pma_ctx* c) {
       PMA_CK(cudaMalloc(&c->d_part[k], sizeof(Partial) * c->work_cap[k]));
     }
     c->nwork[k] = (int)c->h_work[k].size();
-    c->nfin[k] = (int)c->h_fin[k].size();
-    if ((st = ensure_buf(&c->d_fin[k], &c->fin_cap[k], c->h_fin[k].size() + 1)) != PMA_OK)
-      return st;
-    if (c->nfin[k])
-      PMA_CK(cudaMemcpyAsync(c->d_fin[k], c->h_fin[k].data(), sizeof(int) * c->nfin[k],
-                             cudaMemcpyHostToDevice, c->stream));
     if (c->nwork[k])
       PMA_CK(cudaMemcpyAsync(c->d_work[k], c->h_work[k].data(),
                              sizeof(WorkItem) * c->nwork[k], cudaMemcpyHostToDevice,
                              c->stream));
-    // largest items first (ties in list order): the persistent CTAs then
-    // end the launch on the smallest items instead of a few large ones
-    std::vector<int>& ord = c->h_order[k];
-    ord.resize(c->nwork[k]);
-    for (int t = 0; t < c->nwork[k]; ++t) ord[t] = t;
     const std::vector<WorkItem>& wl = c->h_work[k];
     auto size_of = [&](int t) {
       const WorkItem& w = wl[t];
       const long long d = (k == CLS_3D_F32 || k == CLS_3D_F64) ? (w.kz >> 16) : 1;
       return (long long)(w.ext & 0xffff) * (long long)(w.ext >> 16) * d;
     };
-    std::stable_sort(ord.begin(), ord.end(),
-                     [&](int x, int y) { return size_of(x) > size_of(y); });
-    if ((st = ensure_buf(&c->d_order[k], &c->order_cap[k], ord.size() + 1)) != PMA_OK) return st;
-    if (c->nwork[k])
-      PMA_CK(cudaMemcpyAsync(c->d_order[k], ord.data(), sizeof(int) * ord.size(),
-                             cudaMemcpyHostToDevice, c->stream));
     const int per_sm = sweep_max_blocks_per_sm(k, c->tile_id[k]);
-    c->grid[k] = std::min(c->nwork[k], per_sm * c->num_sms);
+    for (int g = 0; g < kGroups; ++g) {
+      const int kg = k * kGroups + g;
+      c->nfin[kg] = (int)c->h_fin[kg].size();
+      if ((st = ensure_buf(&c->d_fin[kg], &c->fin_cap[kg], c->h_fin[kg].size() + 1)) != PMA_OK)
+        return st;
+      if (c->nfin[kg])
+        PMA_CK(cudaMemcpyAsync(c->d_fin[kg], c->h_fin[kg].data(), sizeof(int) * c->nfin[kg],
+                               cudaMemcpyHostToDevice, c->stream));
+      // largest items first (ties in list order), relative to the group's
+      // first item: the persistent CTAs then end the launch on the smallest
+      // items instead of a few large ones
+      std::vector<int>& ord = c->h_order[kg];
+      const int b = c->gbeg[kg], n = c->gcnt[kg];
+      ord.resize(n);
+      for (int t = 0; t < n; ++t) ord[t] = t;
+      std::stable_sort(ord.begin(), ord.end(),
+                       [&](int x, int y) { return size_of(b + x) > size_of(b + y); });
+      if ((st = ensure_buf(&c->d_order[kg], &c->order_cap[kg], ord.size() + 1)) != PMA_OK)
+        return st;
+      if (n)
+        PMA_CK(cudaMemcpyAsync(c->d_order[kg], ord.data(), sizeof(int) * ord.size(),
+                               cudaMemcpyHostToDevice, c->stream));
+      c->grid[kg] = std::min(n, per_sm * c->num_sms);
+    }
   }
   PMA_CK(cudaMemcpyAsync(c->d_probs, c->h_probs.data(), sizeof(ProbDesc) * c->slot_cap,
                          cudaMemcpyHostToDevice, c->stream));
@@ -1028,55 +1091,113 @@ LaunchArgs args_for(pma_ctx* c, int k, int t0, int n) {
   a.subs = c->d_subs;
   a.nb = c->d_nb;
   a.tmap = c->d_tmap;
-  a.err = c->d_queue + 2 * NUM_CLS;
+  a.err = c->d_queue + kErrWord;
   a.stall_bytes = c->opt_test_stall ? 16 : 0;
   a.probs = c->d_probs;
   a.st = c->d_state;
   a.part = c->d_part[k];
-  a.queue = c->d_queue + 2 * k;
-  a.grid = std::min(n, c->grid[k] > 0 ? c->grid[k] : n);
-  // the whole class list in one launch takes the largest items first; the
-  // per-subdomain launches of the plain path take theirs in list order
-  a.order = (t0 == 0 && n == c->nwork[k] && c->launch_mode == PMA_LAUNCH_BATCHED)
-                ? c->d_order[k]
-                : nullptr;
+  a.queue = c->d_queue + 2 * (k * kGroups);
+  a.grid = std::min(n, c->grid[k * kGroups] > 0 ? c->grid[k * kGroups] : n);
+  a.order = nullptr;  // the per-subdomain launches take their items in list order
   return a;
 }
 
-pma_status time_mark(pma_ctx* c) {
+// The launch of group g of class k: its contiguous item range, its queue
+// counters, largest items first.
+LaunchArgs args_for_group(pma_ctx* c, int k, int g) {
+  const int kg = k * kGroups + g;
+  LaunchArgs a = args_for(c, k, c->gbeg[kg], c->gcnt[kg]);
+  a.queue = c->d_queue + 2 * kg;
+  a.grid = std::min(c->gcnt[kg], c->grid[kg] > 0 ? c->grid[kg] : c->gcnt[kg]);
+  a.order = c->d_order[kg];
+  return a;
+}
+
+// Timing events of the timed steps (PMA_OPT_TIME_SWEEPS): one pair per
+// group launch, on the group's stream.
+pma_status time_mark(pma_ctx* c, cudaStream_t s) {
   if (!c->time_this_step || c->tev_used >= (int)c->tev.size()) return PMA_OK;
-  PMA_CK(cudaEventRecordWithFlags(c->tev[c->tev_used++], c->stream,
+  PMA_CK(cudaEventRecordWithFlags(c->tev[c->tev_used++], s,
                                   c->capturing ? cudaEventRecordExternal
                                                : cudaEventRecordDefault));
   return PMA_OK;
 }
 
+int groups_with_work(const pma_ctx* c, int k) {
+  int n = 0;
+  for (int g = 0; g < kGroups; ++g) n += c->gcnt[k * kGroups + g] > 0 ? 1 : 0;
+  return n;
+}
+
 pma_status launch_step(pma_ctx* c) {
   for (int k = 0; k < NUM_CLS; ++k) {
     if (c->nwork[k] == 0) continue;
-    pma_status st = time_mark(c);
-    if (st != PMA_OK) return st;
+    pma_status st;
     if (c->launch_mode == PMA_LAUNCH_PER_SUBDOMAIN) {
+      if (c->time_this_step) c->tev_groups.push_back(1);
+      if ((st = time_mark(c, c->stream)) != PMA_OK) return st;
       for (const SubDesc& sd : c->h_subs) {
         const int n = sd.tile_end - sd.tile_begin;
         if (n <= 0 || c->h_probs[sd.prob].cls != k) continue;
         LaunchArgs a = args_for(c, k, sd.tile_begin, n);
         PMA_CK(launch_sweep(k, c->tile_id[k], a, c->stream));
       }
-    } else {
-      LaunchArgs a = args_for(c, k, 0, c->nwork[k]);
-      PMA_CK(launch_sweep(k, c->tile_id[k], a, c->stream));
+      if ((st = time_mark(c, c->stream)) != PMA_OK) return st;
+      PMA_CK(launch_finish(c->d_fin[k * kGroups], c->nfin[k * kGroups], c->d_subs, c->d_probs,
+                           c->d_state, c->d_part[k], c->d_queue + kErrWord, c->stream));
+      continue;
     }
-    st = time_mark(c);
-    if (st != PMA_OK) return st;
-    PMA_CK(launch_finish(c->d_fin[k], c->nfin[k], c->d_subs, c->d_probs, c->d_state,
-                         c->d_part[k], c->d_queue + 2 * NUM_CLS, c->stream));
+    // one sweep + finish chain per group, each on its own stream
+    if (c->time_this_step) c->tev_groups.push_back(groups_with_work(c, k));
+    for (int g = 0; g < kGroups; ++g) {
+      const int kg = k * kGroups + g;
+      if (c->gcnt[kg] == 0) continue;
+      cudaStream_t s = c->gstream[g];
+      if ((st = time_mark(c, s)) != PMA_OK) return st;
+      PMA_CK(launch_sweep(k, c->tile_id[k], args_for_group(c, k, g), s));
+      if ((st = time_mark(c, s)) != PMA_OK) return st;
+      PMA_CK(launch_finish(c->d_fin[kg], c->nfin[kg], c->d_subs, c->d_probs, c->d_state,
+                           c->d_part[k], c->d_queue + kErrWord, s));
+    }
   }
   return PMA_OK;
 }
 
-// Sweep launches per step (one per class, or one per subdomain in the
-// per-subdomain mode) and finish launches per step (one per class).
+// The band steps of a window: the other groups' streams fork from the
+// context's stream before the first step and join it after the last.
+bool uses_group_streams(const pma_ctx* c) {
+  if (c->launch_mode != PMA_LAUNCH_BATCHED) return false;
+  for (int k = 0; k < NUM_CLS; ++k)
+    for (int g = 1; g < kGroups; ++g)
+      if (c->gcnt[k * kGroups + g] > 0) return true;
+  return false;
+}
+
+pma_status launch_steps(pma_ctx* c, int steps) {
+  const bool fork = uses_group_streams(c);
+  if (fork) {
+    PMA_CK(cudaEventRecord(c->ev_gfork, c->stream));
+    for (int g = 1; g < kGroups; ++g) PMA_CK(cudaStreamWaitEvent(c->gstream[g], c->ev_gfork, 0));
+  }
+  pma_status st = PMA_OK;
+  for (int s = 0; s < steps && st == PMA_OK; ++s) {
+    c->time_this_step = c->opt_time_sweeps > 0 && (s % c->opt_time_sweeps) == 0;
+    st = launch_step(c);
+  }
+  c->time_this_step = false;
+  if (fork) {
+    // joined even after a failed launch, so that a capture can end
+    for (int g = 1; g < kGroups; ++g) {
+      PMA_CK(cudaEventRecord(c->ev_gjoin[g], c->gstream[g]));
+      PMA_CK(cudaStreamWaitEvent(c->stream, c->ev_gjoin[g], 0));
+    }
+  }
+  return st;
+}
+
+// Sweep launches per step (one per class and request group, or one per
+// subdomain in the per-subdomain mode) and finish launches per step (one per
+// class and group).
 int sweeps_per_step(pma_ctx* c) {
   int n = 0;
   for (int k = 0; k < NUM_CLS; ++k) {
@@ -1085,14 +1206,17 @@ int sweeps_per_step(pma_ctx* c) {
       for (const SubDesc& sd : c->h_subs)
         if (sd.tile_end > sd.tile_begin && c->h_probs[sd.prob].cls == k) ++n;
     } else {
-      ++n;
+      n += groups_with_work(c, k);
     }
   }
   return n;
 }
 int finishes_per_step(pma_ctx* c) {
   int n = 0;
-  for (int k = 0; k < NUM_CLS; ++k) n += c->nwork[k] > 0 ? 1 : 0;
+  for (int k = 0; k < NUM_CLS; ++k) {
+    if (c->nwork[k] == 0) continue;
+    n += c->launch_mode == PMA_LAUNCH_PER_SUBDOMAIN ? 1 : groups_with_work(c, k);
+  }
   return n;
 }
 int launches_per_step(pma_ctx* c) { return sweeps_per_step(c) + finishes_per_step(c); }
@@ -1110,7 +1234,7 @@ pma_status run_window(pma_ctx* c, int steps) {
   const int nres = res_launches(c);
   const int nband = launches_per_step(c);
   if (c->opt_time_sweeps) {
-    const size_t need = (size_t)2 * NUM_CLS * steps;
+    const size_t need = (size_t)2 * kGroups * NUM_CLS * steps;
     if (c->tev.size() < need) {
       while (c->tev.size() < need) {
         cudaEvent_t e = nullptr;
@@ -1121,6 +1245,7 @@ pma_status run_window(pma_ctx* c, int steps) {
     }
   }
   c->tev_used = 0;
+  if (!graphs) c->tev_groups.clear();
   PMA_CK(cudaEventRecord(c->ev0, c->stream));
   if (nres > 0) {
     pma_status st = launch_res_window(c, steps);
@@ -1135,15 +1260,11 @@ pma_status run_window(pma_ctx* c, int steps) {
         c->gexec = nullptr;
       }
       cudaGraph_t g = nullptr;
+      c->tev_groups.clear();
       PMA_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      pma_status st = PMA_OK;
       c->capturing = true;
-      for (int s = 0; s < steps && st == PMA_OK; ++s) {
-        c->time_this_step = c->opt_time_sweeps > 0 && (s % c->opt_time_sweeps) == 0;
-        st = launch_step(c);
-      }
+      pma_status st = launch_steps(c, steps);
       c->capturing = false;
-      c->time_this_step = false;
       c->graph_steps_timed = c->tev_used;
       cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
       if (st != PMA_OK) {
@@ -1160,12 +1281,8 @@ pma_status run_window(pma_ctx* c, int steps) {
     c->tev_used = c->graph_steps_timed;
     PMA_CK(cudaGraphLaunch(c->gexec, c->stream));
   } else {
-    for (int s = 0; s < steps; ++s) {
-      c->time_this_step = c->opt_time_sweeps > 0 && (s % c->opt_time_sweeps) == 0;
-      pma_status st = launch_step(c);
-      c->time_this_step = false;
-      if (st != PMA_OK) return st;
-    }
+    pma_status st = launch_steps(c, steps);
+    if (st != PMA_OK) return st;
   }
   if (nres > 0) {
     pma_status st = join_res_window(c);
@@ -1174,13 +1291,13 @@ pma_status run_window(pma_ctx* c, int steps) {
   PMA_CK(cudaEventRecord(c->ev1, c->stream));
   PMA_CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(ProbState) * c->slot_cap,
                          cudaMemcpyDeviceToHost, c->stream));
-  PMA_CK(cudaMemcpyAsync(&c->h_err, c->d_queue + 2 * NUM_CLS, sizeof(unsigned int),
+  PMA_CK(cudaMemcpyAsync(&c->h_err, c->d_queue + kErrWord, sizeof(unsigned int),
                          cudaMemcpyDeviceToHost, c->stream));
   PMA_CK(cudaStreamSynchronize(c->stream));
   if (c->h_err != 0) {
     // clear the word so that the context can run again
     c->h_err = 0;
-    PMA_CK(cudaMemsetAsync(c->d_queue + 2 * NUM_CLS, 0, sizeof(unsigned int), c->stream));
+    PMA_CK(cudaMemsetAsync(c->d_queue + kErrWord, 0, sizeof(unsigned int), c->stream));
     PMA_CK(cudaStreamSynchronize(c->stream));
     set_err("a sweep kernel gave up waiting for its staging copies (bounded wait)");
     return PMA_ERR_TIMEOUT;
@@ -1189,12 +1306,24 @@ pma_status run_window(pma_ctx* c, int steps) {
   PMA_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   c->stats.windows += 1;
   c->stats.window_ms += ms;
-  for (int i = 0; i + 1 < c->tev_used; i += 2) {
-    float km = 0.f;
-    PMA_CK(cudaEventElapsedTime(&km, c->tev[i], c->tev[i + 1]));
-    c->stats.sweep_kernel_ms += km;
+  // timed (step, class) pairs: from the first group's sweep start to the
+  // latest sweep end (the groups' sweeps run at the same time)
+  for (size_t q = 0, i = 0; q < c->tev_groups.size(); ++q) {
+    const int ng = c->tev_groups[q];
+    if ((int)i + 2 * ng > c->tev_used) break;
+    float lo = 0.f, hi = 0.f;
+    for (int g = 0; g < ng; ++g) {
+      float t0 = 0.f, t1 = 0.f;
+      if (g > 0) PMA_CK(cudaEventElapsedTime(&t0, c->tev[i], c->tev[i + 2 * g]));
+      PMA_CK(cudaEventElapsedTime(&t1, c->tev[i], c->tev[i + 2 * g + 1]));
+      lo = std::min(lo, t0);
+      hi = std::max(hi, t1);
+    }
+    i += 2 * ng;
+    c->stats.sweep_kernel_ms += hi - lo;
     c->stats.sweep_kernel_launches += 1;
   }
+  for (int k = 0; k < NUM_CLS; ++k) c->stats.sweep_steps += c->nwork[k] > 0 ? steps : 0;
   c->stats.sweep_launches += (int64_t)steps * sweeps_per_step(c) + nres;
   c->stats.other_launches += (int64_t)steps * finishes_per_step(c);
   c->stats.res_launches += nres;
@@ -1427,8 +1556,14 @@ pma_status pma_create(pma_ctx** out, int device, size_t mem_budget_bytes, void* 
   pma_status st = ensure_slots(c.get(), 64);
   if (st != PMA_OK) return st;
   PMA_CK(cudaMalloc(&c->d_check, sizeof(double) * 4 + sizeof(unsigned long long)));
-  PMA_CK(cudaMalloc(&c->d_queue, sizeof(unsigned int) * (2 * NUM_CLS + 1)));
-  PMA_CK(cudaMemset(c->d_queue, 0, sizeof(unsigned int) * (2 * NUM_CLS + 1)));
+  PMA_CK(cudaMalloc(&c->d_queue, sizeof(unsigned int) * (kErrWord + 1)));
+  PMA_CK(cudaMemset(c->d_queue, 0, sizeof(unsigned int) * (kErrWord + 1)));
+  c->gstream[0] = c->stream;
+  for (int g = 1; g < kGroups; ++g) {
+    PMA_CK(cudaStreamCreateWithFlags(&c->gstream[g], cudaStreamNonBlocking));
+    PMA_CK(cudaEventCreateWithFlags(&c->ev_gjoin[g], cudaEventDisableTiming));
+  }
+  PMA_CK(cudaEventCreateWithFlags(&c->ev_gfork, cudaEventDisableTiming));
   PMA_CK(cudaEventCreate(&c->ev0));
   PMA_CK(cudaEventCreate(&c->ev1));
   *out = c.release();
@@ -1454,9 +1589,11 @@ pma_status pma_destroy(pma_ctx* c) {
   cudaFree(c->d_tmap);
   for (int k = 0; k < NUM_CLS; ++k) {
     cudaFree(c->d_work[k]);
-    cudaFree(c->d_order[k]);
     cudaFree(c->d_part[k]);
-    cudaFree(c->d_fin[k]);
+  }
+  for (int kg = 0; kg < NUM_CLS * kGroups; ++kg) {
+    cudaFree(c->d_order[kg]);
+    cudaFree(c->d_fin[kg]);
   }
   cudaFree(c->d_jobs);
   cudaFree(c->d_stage);
@@ -1475,6 +1612,14 @@ pma_status pma_destroy(pma_ctx* c) {
     if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  for (int g = 1; g < kGroups; ++g) {
+    if (c->gstream[g]) {
+      cudaStreamSynchronize(c->gstream[g]);
+      cudaStreamDestroy(c->gstream[g]);
+    }
+    if (c->ev_gjoin[g]) cudaEventDestroy(c->ev_gjoin[g]);
+  }
+  if (c->ev_gfork) cudaEventDestroy(c->ev_gfork);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return PMA_OK;
@@ -1492,6 +1637,12 @@ pma_status pma_set_option(pma_ctx* c, int32_t opt, int64_t v) {
     case PMA_OPT_LAUNCH_MODE:
       if (v != PMA_LAUNCH_BATCHED && v != PMA_LAUNCH_PER_SUBDOMAIN) return PMA_ERR_INVALID;
       c->launch_mode = (int)v;
+      c->dirty = true;  // the request groups depend on the launch mode
+      break;
+    case PMA_OPT_GROUPS:
+      if (v < 1 || v > kGroups) return PMA_ERR_INVALID;
+      c->ngroups = (int)v;
+      c->dirty = true;
       break;
     case PMA_OPT_TILE_2D:
       if (v < 0 || v >= tile2d_count()) return PMA_ERR_INVALID;
@@ -1543,6 +1694,7 @@ pma_status pma_get_option(pma_ctx* c, int32_t opt, int64_t* v) {
     case PMA_OPT_TIME_SWEEPS: *v = c->opt_time_sweeps; break;
     case PMA_OPT_RESIDENT_STEPS: *v = c->opt_res_steps; break;
     case PMA_OPT_TEST_STALL: *v = c->opt_test_stall; break;
+    case PMA_OPT_GROUPS: *v = c->ngroups; break;
     default: return PMA_ERR_INVALID;
   }
   return PMA_OK;

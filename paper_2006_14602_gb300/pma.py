@@ -48,6 +48,7 @@ PMA_OPT_RESIDENT = 7
 PMA_OPT_TIME_SWEEPS = 8
 PMA_OPT_RESIDENT_STEPS = 9
 PMA_OPT_TEST_STALL = 10
+PMA_OPT_GROUPS = 11
 PMA_LAUNCH_BATCHED = 0
 PMA_LAUNCH_PER_SUBDOMAIN = 1
 
@@ -106,7 +107,7 @@ class pma_stats(C.Structure):
                 ("res_launches", C.c_int64), ("res_node_updates", C.c_int64),
                 ("sweep_kernel_ms", C.c_double), ("sweep_kernel_launches", C.c_int64),
                 ("admit_ms", C.c_double), ("rebuild_ms", C.c_double),
-                ("combine_ms", C.c_double)]
+                ("combine_ms", C.c_double), ("sweep_steps", C.c_int64)]
 
 
 _lib = None
@@ -416,7 +417,8 @@ class Context:
              "launch_mode": PMA_OPT_LAUNCH_MODE, "tile_2d": PMA_OPT_TILE_2D,
              "tile_3d": PMA_OPT_TILE_3D, "max_active": PMA_OPT_MAX_ACTIVE,
              "resident": PMA_OPT_RESIDENT, "time_sweeps": PMA_OPT_TIME_SWEEPS,
-             "resident_steps": PMA_OPT_RESIDENT_STEPS, "test_stall": PMA_OPT_TEST_STALL}
+             "resident_steps": PMA_OPT_RESIDENT_STEPS, "test_stall": PMA_OPT_TEST_STALL,
+             "groups": PMA_OPT_GROUPS}
 
     def set(self, name: str, value: int):
         st = pma_set_option(self.h, self._OPTS[name], int(value))
