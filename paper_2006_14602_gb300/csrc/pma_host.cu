@@ -2283,11 +2283,16 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
   la.order = nullptr;
   la.grid = std::min(la.nwork, sweep_max_blocks_per_sm(cls, 0) * num_sms);
 
-  // step in windows until the request is done (two extra launches cover
-  // the initial-state and theta^0 passes)
-  const int window = 64;
-  for (;;) {
-    for (int k = 0; k < window; ++k) {
+  // step in windows until the request is done: the first window also
+  // covers the initial-state and theta^0 passes; windows then double (16 up
+  // to 256 steps) and never run past the step cap, so a request that stops
+  // early is followed by at most one window of launches that skip it
+  const long long cap = r.p.max_steps;
+  long long taken = 0;  // steps taken at the last read-back
+  long long w = 16;
+  for (bool first = true;; first = false) {
+    const long long n = std::min(w, std::max(1LL, cap - taken)) + (first ? 2 : 0);
+    for (long long k = 0; k < n; ++k) {
       PMA_CK(launch_sweep(cls, 0, la, s));
       PMA_CK(launch_finish((const int*)(B + o_fin), 1, la.subs, la.probs, la.st, la.part, la.err,
                            s));
@@ -2295,6 +2300,8 @@ extern "C" pma_status pma_solve_static(const pma_grid* grid, const pma_monitor* 
     PMA_CK(cudaMemcpyAsync(&ps, B + o_st, sizeof(ps), cudaMemcpyDeviceToHost, s));
     PMA_CK(cudaStreamSynchronize(s));
     if (ps.phase == PH_DONE) break;
+    taken = ps.step;
+    w = std::min(2 * w, 256LL);
   }
 
   // owner-takes combination into the caller's buffer
