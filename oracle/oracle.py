@@ -97,6 +97,10 @@ def _bind(lib):
                              P(C.c_double), P(C.c_double), P(C.c_double),
                              P(C.c_double), P(_Info)]
     lib.or_solve.restype = C.c_int
+    lib.or_solve_det.argtypes = [P(_Grid), P(_Monitor), P(_Decomp), P(_Params),
+                                 P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_double),
+                                 P(C.c_double), P(_Info)]
+    lib.or_solve_det.restype = C.c_int
     lib.or_monitor_eval.argtypes = [P(_Monitor), C.c_int, P(C.c_double), C.c_long,
                                     P(C.c_double)]
     lib.or_monitor_eval.restype = C.c_int
@@ -187,14 +191,16 @@ class OracleResult:
     theta: float
     min_det: float
     status: str
+    det: Optional[np.ndarray] = None   # owner-stencil det D_h^2 Psi (want_det)
 
 
 def _shape(prob):
     return tuple(int(prob.n[a]) for a in reversed(range(prob.dim)))
 
 
-def solve(prob, psi0: Optional[np.ndarray] = None) -> OracleResult:
-    """Run the oracle on a problem (attributes as in the input module)."""
+def solve(prob, psi0: Optional[np.ndarray] = None, want_det: bool = False) -> OracleResult:
+    """Run the oracle on a problem (attributes as in the input module);
+    want_det also returns det D_h^2 Psi of each global node's owner stencil."""
     lib = _load()
     g = _grid(prob)
     m = _monitor(prob.monitor)
@@ -218,13 +224,15 @@ def solve(prob, psi0: Optional[np.ndarray] = None) -> OracleResult:
     p0 = None
     if psi0 is not None:
         p0 = np.ascontiguousarray(psi0, dtype=np.float64).reshape(N)
-    rc = lib.or_solve(C.byref(g), C.byref(m), C.byref(d), C.byref(p), _dptr(p0),
-                      _dptr(x), _dptr(psi), _dptr(hist), C.byref(info))
+    det = np.zeros(shape, dtype=np.float64) if want_det else None
+    rc = lib.or_solve_det(C.byref(g), C.byref(m), C.byref(d), C.byref(p), _dptr(p0),
+                          _dptr(x), _dptr(psi), _dptr(det), _dptr(hist), C.byref(info))
     if rc in (-1, -2):
         raise ValueError("oracle rejected the problem (status %d)" % rc)
     return OracleResult(x=x, psi=psi, res=hist[: info.steps].copy(), steps=int(info.steps),
                         residual=float(info.residual), theta=float(info.theta),
-                        min_det=float(info.min_det), status=STATUS[int(info.status)])
+                        min_det=float(info.min_det), status=STATUS[int(info.status)],
+                        det=det)
 
 
 def operator(prob, v: np.ndarray):

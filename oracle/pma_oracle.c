@@ -406,8 +406,10 @@ static int is_owned(const sub_t *s, int dim, const long *gidx) {
   return 1;
 }
 
-/* Combined output (owner-takes): x_g = grad_h Psi of the owning subdomain. */
-static void dd_output(const dd_t *d, int use_new, double *x_out, double *psi_out) {
+/* Combined output (owner-takes): x_g = grad_h Psi of the owning subdomain,
+ * and optionally det D_h^2 Psi from the same (owner's) stencil.            */
+static void dd_output(const dd_t *d, int use_new, double *x_out, double *psi_out,
+                      double *det_out) {
   long gi, gj, gl;
   long Ntot = d->N[0] * d->N[1] * d->N[2];
   for (gl = 0; gl < d->N[2]; ++gl)
@@ -424,6 +426,7 @@ static void dd_output(const dd_t *d, int use_new, double *x_out, double *psi_out
         node_op(d, s, v, i, j, l, x, H);
         if (x_out)
           for (a = 0; a < d->dim; ++a) x_out[a * Ntot + gflat] = x[a];
+        if (det_out) det_out[gflat] = det_sym(d->dim, H);
         if (psi_out) {
           double q = 0.0;
           for (a = 0; a < d->dim; ++a) {
@@ -438,6 +441,12 @@ static void dd_output(const dd_t *d, int use_new, double *x_out, double *psi_out
 int or_solve(const or_grid *g, const or_monitor *m, const or_decomp *ddp,
              const or_params *p, const double *psi0, double *x_out,
              double *psi_out, double *res_hist, or_info *info) {
+  return or_solve_det(g, m, ddp, p, psi0, x_out, psi_out, NULL, res_hist, info);
+}
+
+int or_solve_det(const or_grid *g, const or_monitor *m, const or_decomp *ddp,
+                 const or_params *p, const double *psi0, double *x_out,
+                 double *psi_out, double *det_out, double *res_hist, or_info *info) {
   dd_t d;
   or_decomp one = {{1, 1, 1}, 0, 0, 1};
   int rc, s, status = OR_NOT_CONVERGED, a;
@@ -604,7 +613,7 @@ int or_solve(const or_grid *g, const or_monitor *m, const or_decomp *ddp,
     }
   }
 
-  dd_output(&d, 0, x_out, psi_out);
+  dd_output(&d, 0, x_out, psi_out, det_out);
   if (info) {
     info->steps = steps;
     info->residual = last_res;

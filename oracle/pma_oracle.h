@@ -130,6 +130,13 @@ int or_solve(const or_grid *g, const or_monitor *m, const or_decomp *dd,
              const or_params *p, const double *psi0, double *x_out,
              double *psi_out, double *res_hist, or_info *info);
 
+/* or_solve, and det_out (optional, N values): det D_h^2 Psi at every global
+ * node from the stencil of the node's owner, the stencil the combined mesh
+ * is taken from.                                                          */
+int or_solve_det(const or_grid *g, const or_monitor *m, const or_decomp *dd,
+                 const or_params *p, const double *psi0, double *x_out,
+                 double *psi_out, double *det_out, double *res_hist, or_info *info);
+
 /* rho at npts points x (point-major, dim values each). */
 int or_monitor_eval(const or_monitor *m, int dim, const double *x, long npts,
                     double *rho_out);

@@ -47,19 +47,21 @@ def test_check_matches_oracle_on_a_single_domain(dim):
 
 def test_check_on_decomposed_requests():
     """Decomposed requests: the cell measures of the combined (owner-takes)
-    mesh equal the oracle's; det is taken with each node's owner stencil on
-    the device and with the global stencil by the oracle's quality measure,
-    so only its sign is compared.  A request that tangled returns the last
+    mesh equal the oracle's, and min det (each global node's det D_h^2 Psi
+    from its owner's stencil, in FP64) equals the minimum of the oracle's
+    owner-stencil determinants.  A request that tangled returns the last
     valid state: the tangling can sit in an overlap copy that the combined
     mesh does not use, so its combined mesh stays valid, as the oracle's."""
     prob = W.Problem(dim=2, n=(45, 37, 1), monitor=W.ring_monitor(), parts=(3, 2, 1), overlap=5,
                      dt=W.dt_for((45, 37, 1), 2), tol=0.0, max_steps=150, precision="fp64")
     bad = W.small_case(2, 25, parts=(2, 2, 1), overlap=4, steps=400).replace(
         dt=W.dt_for((25, 25, 1), 2, cfl=4.0))
-    for p in (prob, bad):
-        ref = oracle.solve(p)
+    alt = prob.replace(alternating=1, exchange_every=3)
+    for p in (prob, bad, alt):
+        ref = oracle.solve(p, want_det=True)
         q = oracle.quality(p, ref.psi)
         out = _check_request(p)
         assert abs(out[2] - q["min_cell"]) <= 1e-9 * abs(q["min_cell"])
         assert (out[3] == 0) == (q["min_cell"] > 0)
-        assert (out[0] > 0) == (q["min_det"] > 0)
+        dmin = float(ref.det.min())
+        assert abs(out[0] - dmin) <= 1e-9 * abs(dmin), (out[0], dmin)

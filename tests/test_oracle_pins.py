@@ -714,3 +714,31 @@ def test_frozen_interface_data_hold_between_exchanges():
             np.testing.assert_array_equal(a.psi, b.psi)
         else:
             assert np.abs(a.psi - b.psi).max() > 0
+
+
+def test_owner_stencil_determinant_output():
+    """The oracle's det output is det D_h^2 Psi at each global node from its
+    owner's stencil: on one domain it equals the operator applied to the
+    combined Psi everywhere; on blocks, wherever a node's 3 x 3 stencil lies
+    in its owner's core (so the combined Psi holds the owner's values)."""
+    single = W.small_case(2, 23, steps=40)
+    r = oracle.solve(single, want_det=True)
+    xs = np.meshgrid(*_xi(single), indexing="xy")
+    v = r.psi - 0.5 * (xs[0] ** 2 + xs[1] ** 2)
+    _, det, _, _ = oracle.operator(single, v)
+    np.testing.assert_allclose(r.det, det, rtol=0, atol=1e-12)
+    dd = single.replace(parts=(2, 2, 1), overlap=4)
+    r = oracle.solve(dd, want_det=True)
+    v = r.psi - 0.5 * (xs[0] ** 2 + xs[1] ** 2)
+    _, det, _, _ = oracle.operator(dd, v)
+    _, _, clo, chi = oracle.extents(23, 2, 4)
+    own = np.searchsorted(chi, np.arange(23))          # core index per axis
+    same = np.ones((23, 23), dtype=bool)
+    for dj in (-1, 0, 1):
+        for di in (-1, 0, 1):
+            jj = np.clip(np.arange(23) + dj, 0, 22)
+            ii = np.clip(np.arange(23) + di, 0, 22)
+            same &= (own[jj][:, None] == own[:, None]) & (own[ii][None, :] == own[None, :])
+    assert same.sum() > 300 and (~same).sum() > 50
+    np.testing.assert_allclose(r.det[same], det[same], rtol=0, atol=1e-12)
+    assert np.abs(r.det - det).max() > 1e-9   # the overlap copies do differ
