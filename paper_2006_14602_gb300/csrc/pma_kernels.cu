@@ -918,6 +918,17 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
     const int t = s_t[b];
     if (t >= tend) break;
     if (tid == 0) {
+      // the band's TMA box first, so that its copy overlaps the prefetch of
+      // the following item (whose queue atomic this thread then waits for)
+      const BandHdr<T>& Hc = HB[b];
+      const int pc = Hc.ps.phase;
+      if (pc != PH_DONE && pc != PH_INIT_V && a.tmap != nullptr && Hc.w.tma_rows > 0) {
+        const int swp = (((Hc.w.ext & 0xffff) + 3) & ~3) + 8;
+        fence_proxy_async();
+        mbar_expect_tx(&tbar, (unsigned int)(swp * Hc.w.tma_rows * (int)sizeof(T) + a.stall_bytes));
+        tma_load_2d(sv, (const char*)a.tmap + 128 * ((size_t)Hc.w.tma_map + Hc.ps.parity),
+                    (Hc.w.ij & 0xffff) - 4, (Hc.w.ij >> 16) - 1, &tbar);
+      }
       // publish and prefetch the following item into the other buffer
       s_t[b ^ 1] = t_next;
       if (t_next < tend) {
@@ -983,12 +994,7 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
       //     the pitched row skipped, rows mirrored / clamped).
       const int SHT = tr > 0 ? tr : SH;
       if (tr > 0) {
-        if (tid == 0) {
-          fence_proxy_async();
-          mbar_expect_tx(&tbar, (unsigned int)(SWp * tr * (int)sizeof(T) + a.stall_bytes));
-          tma_load_2d(sv, (const char*)a.tmap + 128 * ((size_t)H.w.tma_map + H.ps.parity),
-                      i0 - 4, j0 - 1, &tbar);
-        }
+        // the box was issued right after S1
       } else {
         for (int e = tid; e < SH * cpr; e += NT) {
           const int r = qdiv(e, cpr, inv_cpr), k = e - r * cpr;
@@ -1704,6 +1710,18 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
     const int t = s_t[b];
     if (t >= tend) break;
     if (tid == 0) {
+      // the box's TMA copy first, so that it overlaps the prefetch of the
+      // following item (whose queue atomic this thread then waits for)
+      const SmemHdr<T>& Hc = HB[b];
+      const int pc = Hc.ps.phase;
+      if (pc != PH_DONE && pc != PH_INIT_V && a.tmap != nullptr && Hc.w.tma_rows > 0) {
+        const int swp = (((Hc.w.ext & 0xffff) + 3) & ~3) + 8;
+        const int shy = (Hc.w.ext >> 16) + 2, shz = (Hc.w.kz >> 16) + 2;
+        fence_proxy_async();
+        mbar_expect_tx(&tbar, (unsigned int)(swp * shy * shz * (int)sizeof(T) + a.stall_bytes));
+        tma_load_3d(sv, (const char*)a.tmap + 128 * ((size_t)Hc.w.tma_map + Hc.ps.parity),
+                    (Hc.w.ij & 0xffff) - 4, (Hc.w.ij >> 16) - 1, (Hc.w.kz & 0xffff) - 1, &tbar);
+      }
       s_t[b ^ 1] = t_next;
       if (t_next < tend) {
         issue_hdr<T>(a, HB[b ^ 1], w_next);
@@ -1772,12 +1790,7 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
       //     else 16-byte asynchronous copies of every staged row
       const bool tma = a.tmap != nullptr && H.w.tma_rows > 0;
       if (tma) {
-        if (tid == 0) {
-          fence_proxy_async();
-          mbar_expect_tx(&tbar, (unsigned int)(PS * SHZ * (int)sizeof(T) + a.stall_bytes));
-          tma_load_3d(sv, (const char*)a.tmap + 128 * ((size_t)H.w.tma_map + H.ps.parity),
-                      i0 - 4, j0 - 1, k0 - 1, &tbar);
-        }
+        // the box was issued right after the header barrier
       } else {
         for (int e = tid; e < nrow * cpr; e += NT) {
           const int rr = qdiv(e, cpr, inv_cpr), k = e - rr * cpr;
