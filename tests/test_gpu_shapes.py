@@ -2,10 +2,11 @@
 
 The autotuner (and so the benchmark) may pick any compiled shape: bands of
 768 to 6144 nodes with register budgets of 6 or 7 CTAs per SM in 2D, boxes
-of 512 nodes per plane with budgets of 3 to 6 CTAs per SM in 3D (the
-smaller budgets spill a little).  Each one must meet the parity bounds on
-subdomains that it cuts into several bands or boxes (ragged last band,
-transmission rows and columns inside the band perimeter)."""
+of 512 nodes per plane over 8 planes with budgets of 3 to 6 CTAs per SM in
+3D (the smaller budgets spill a little).  Each one must
+meet the parity bounds on subdomains that it cuts into several bands or
+boxes (ragged last band, transmission rows and columns inside the band
+perimeter)."""
 import numpy as np
 import pytest
 
