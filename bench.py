@@ -547,6 +547,10 @@ def native(args, rank, world, device):
         "e2e_host_ms": {k: sum(getattr(s, k) for s in e2e_stats) / len(e2e_stats)
                         for k in ("admit_ms", "rebuild_ms", "combine_ms")},
         "meshes": len(probs) * args.steps, "lat": lat, "wall_s": t_wall,
+        # global-node updates (each node of a request's global grid once per
+        # step it took, overlap copies not counted)
+        "global_nu": sum(p.nodes * st for p, st in zip(probs, [i["steps"] for i in infos]))
+                     * args.steps,
         "infos_steps": [i["steps"] for i in infos],
         "tuned": tuned, "window": opts["window_steps"],
     }
@@ -694,6 +698,7 @@ def main():
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "meshes_per_s": a0["meshes"] / (a0["ms"] / 1e3),
+        "global_node_updates_per_s": sum(a["global_nu"] for a in agg) / (ms / 1e3),
         "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99),
                        "what": "per request, submit to completion, all requests of a "
                                "step submitted together"},

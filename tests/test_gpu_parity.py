@@ -153,6 +153,26 @@ def test_warm_start():
     assert np.abs(x - ref.x).max() <= TOL64
 
 
+def test_resume_from_the_returned_psi():
+    """Checkpoint / resume through the warm start of Sect. 2: on one domain
+    the combined Psi after n steps is the whole state, so n steps, then m
+    more from the returned Psi, give the mesh of one n + m-step run.  On
+    blocks the restart also resets the transmission nodes to their owners'
+    current values (the uninterrupted parallel run holds the previous
+    ones), exactly as the oracle's restart does."""
+    one = W.Problem(dim=2, n=(41, 37, 1), monitor=W.ring_monitor(), dt=W.dt_for((41, 37, 1), 2),
+                    tol=0.0, max_steps=300, precision="fp64")
+    for prob in (one, one.replace(parts=(2, 2, 1), overlap=4)):
+        _, psi, _ = pma.solve(prob)
+        x2, _, i2 = pma.solve(prob.replace(max_steps=200), psi0=psi)
+        assert i2.steps == 200
+        ref = oracle.solve(prob.replace(max_steps=200), psi0=oracle.solve(prob).psi)
+        assert np.abs(x2 - ref.x).max() <= TOL64
+        if prob.parts == (1, 1, 1):
+            x, _, _ = pma.solve(prob.replace(max_steps=500))
+            assert np.abs(x2 - x).max() <= TOL64
+
+
 def test_tangle_is_reported_with_last_valid_mesh():
     prob = W.small_case(2, 25, parts=(2, 2, 1), overlap=4, steps=400).replace(
         dt=W.dt_for((25, 25, 1), 2, cfl=4.0))
