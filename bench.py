@@ -58,7 +58,7 @@ WORKLOADS = {
              "FP64 residual/stop test, 2000 steps; 166 MB of state (larger than L2)",
     "c4x2": "uneven batch twice over: 1024 independent 2D problems (seeds 14602 and 14603), "
             "sides log-uniform in [17,513], 1-16 subdomains (overlap 4-8), 1-4 Gaussian "
-            "bumps/rings, FP32, tol 1e-6 or 2000 steps; 197 MB of state (larger than L2)",
+            "bumps/rings, FP32, tol 1e-6 or 2000 steps; 213 MB of state (larger than L2)",
 }
 
 
