@@ -603,7 +603,9 @@ __device__ __forceinline__ RunK<T> make_runk(const ProbHot<T>& ph, const ProbSta
   K.logrhs = ph.rhs == PMA_RHS_LOG || phase != PH_RUN;
   K.scale_root = K.inv_dim = T(0);
   if (!K.logrhs) {
-    K.scale_root = (T)(ph.vol / (T)ps.theta_prev);
+    // (|Omega_c| rho det / theta)^(1/d) - 1 with the global normalisation,
+    // (rho det)^(1/d) - 1 without it
+    K.scale_root = ph.normalize == PMA_NORM_GLOBAL_THETA ? (T)(ph.vol / (T)ps.theta_prev) : T(1);
     K.inv_dim = T(1) / (T)ph.dim;
   }
   K.lo0 = ph.lo[0];

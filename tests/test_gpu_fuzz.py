@@ -1,0 +1,93 @@
+"""Seeded random problems against the FP64 oracle: every option of the
+problem statement drawn at random (2D / 3D, grid sizes and domains,
+decompositions and overlaps, parallel or alternating transmission,
+exchange_every, log or root form, both stop norms and rules, check_every,
+normalisation on or off, monitor kinds, FP64 or FP32), all of them in one
+batched context next to each other, each compared node by node with the
+oracle after the same steps (FP64 1e-11, FP32 1e-5 of the domain size) with
+the same step count and status."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_14602_gb300 import pma
+from paper_2006_14602_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _parts(rng, n, o):
+    # largest admissible count: every core holds at least ceil(o/2) + 2 nodes
+    pmax = max(1, min(4, n // (o // 2 + o - o // 2 + 3)))
+    return int(rng.integers(1, pmax + 1))
+
+
+def _problem(rng):
+    dim = 2 if rng.uniform() < 0.7 else 3
+    side = (9, 48) if dim == 2 else (7, 20)
+    n = [int(rng.integers(side[0], side[1])) for _ in range(dim)]
+    lo = [float(rng.uniform(-0.5, 0.5)) for _ in range(dim)]
+    hi = [lo[a] + float(rng.uniform(0.6, 1.6)) for a in range(dim)]
+    o = int(rng.integers(2, 7))
+    parts = [_parts(rng, n[a], o) for a in range(dim)]
+    if all(p == 1 for p in parts):
+        o = 0
+    centre = tuple(lo[a] + 0.5 * (hi[a] - lo[a]) for a in range(dim)) + (0.5,) * (3 - dim)
+    kind = rng.integers(0, 3)
+    if kind == 0:
+        mon = W.random_bumps(rng, dim)
+        # centres inside this problem's box
+        for t in mon.terms:
+            t.c = tuple(lo[a] + (t.c[a] - 0.2) / 0.6 * (hi[a] - lo[a]) if a < dim else 0.5
+                        for a in range(3))
+    elif kind == 1:
+        mon = W.ring_monitor(dim, amp=float(rng.uniform(2, 12)), width=float(rng.uniform(10, 60)),
+                             r2=float(rng.uniform(0.01, 0.06)), centre=centre)
+    else:
+        f = [(float(rng.uniform(1, 5)), float(rng.uniform(5, 30)),
+              lo[a] + float(rng.uniform(0.3, 0.7)) * (hi[a] - lo[a])) for a in range(dim)]
+        mon = W.product_monitor(f)
+    rhs = "root" if rng.uniform() < 0.25 else "log"
+    prec = str(rng.choice(["fp64", "fp32"]))
+    # a tolerance only where both sides see the same residual to rounding
+    tol = float(rng.choice([0.0, 1e-3])) if prec == "fp64" else 0.0
+    nn = tuple(n) + (1,) * (3 - dim)
+    cfl = (0.06 if dim == 2 else 0.03) * float(rng.uniform(0.5, 1.0))
+    h2 = min(((hi[a] - lo[a]) / (n[a] - 1)) ** 2 for a in range(dim))
+    return W.Problem(
+        dim=dim, n=nn, lo=tuple(lo) + (0.0,) * (3 - dim), hi=tuple(hi) + (1.0,) * (3 - dim),
+        monitor=mon, parts=tuple(parts) + (1,) * (3 - dim), overlap=o,
+        alternating=int(rng.uniform() < 0.3), exchange_every=int(rng.choice([1, 1, 2, 3])),
+        dt=cfl * h2, tol=tol,
+        max_steps=int(rng.integers(5, 90)),
+        stop_norm=str(rng.choice(["max_ut", "l2_increment"])),
+        stop_rule=str(rng.choice(["all", "any"])), check_every=int(rng.choice([1, 1, 3])),
+        rhs=rhs, lag_theta=1 if rhs == "root" else 0,
+        normalize="none" if rng.uniform() < 0.2 else "global_theta",
+        precision=prec)
+
+
+def test_random_problems_in_one_batch():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2006_14602_gb300 import build
+    build.build()
+    pma.load()
+    rng = np.random.default_rng(20061460)
+    probs = [_problem(rng) for _ in range(48)]
+    refs = oracle.solve_parallel([p.replace(precision="fp64") for p in probs])
+    res = pma.solve_many(probs, window_steps=16)
+    kinds = set()
+    for i, (p, ref, (x, _, info)) in enumerate(zip(probs, refs, res)):
+        kinds.add((p.dim, p.precision, p.alternating, p.exchange_every > 1, p.rhs))
+        if p.precision == "fp64" or ref.status != "tangled":
+            assert info.steps == ref.steps, (i, info.steps, ref.steps)
+        if p.precision == "fp64":
+            assert pma.STATUS_NAMES[info.status] == ref.status, i
+        size = max(p.hi[a] - p.lo[a] for a in range(p.dim))
+        tol = 1e-11 if p.precision == "fp64" else 1e-5
+        if ref.status != "tangled":
+            assert np.abs(x - ref.x).max() <= tol * size, (i, np.abs(x - ref.x).max())
+    assert len(kinds) >= 12

@@ -129,7 +129,7 @@ def test_spiral_monitor_short():
     _check(prob)
 
 
-@pytest.mark.parametrize("variant", ["l2", "any", "check7", "none", "root"])
+@pytest.mark.parametrize("variant", ["l2", "any", "check7", "none", "root", "root_none"])
 def test_stop_rules_and_variants(variant):
     base = W.Problem(dim=2, n=(29, 29, 1), monitor=W.ring_monitor(), parts=(2, 2, 1), overlap=4,
                      dt=W.dt_for((29, 29, 1), 2), tol=2e-4, max_steps=3000, precision="fp64")
@@ -137,9 +137,13 @@ def test_stop_rules_and_variants(variant):
             "any": base.replace(stop_rule="any"),
             "check7": base.replace(check_every=7),
             "none": base.replace(normalize="none", tol=0.0, max_steps=200),
-            "root": base.replace(rhs="root", lag_theta=1)}[variant]
+            "root": base.replace(rhs="root", lag_theta=1),
+            # the root form of the unnormalised subdomain equations:
+            # (rho det)^(1/d) - 1
+            "root_none": base.replace(rhs="root", lag_theta=1, normalize="none", tol=0.0,
+                                      max_steps=200)}[variant]
     x, p, info, ref, err = _check(prob)
-    if variant != "none":
+    if variant not in ("none", "root_none"):
         assert info.status == pma.PMA_OK
     assert abs(info.residual - ref.residual) <= 1e-8 * max(ref.residual, 1e-300)
 
