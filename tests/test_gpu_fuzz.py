@@ -2,7 +2,9 @@
 problem statement drawn at random (2D / 3D, grid sizes and domains,
 decompositions and overlaps, parallel or alternating transmission,
 exchange_every, log or root form, both stop norms and rules, check_every,
-normalisation on or off, monitor kinds, FP64 or FP32), all of them in one
+normalisation on or off, monitor kinds (bump/ring sums, separable
+products, tables, an arc-length density), warm starts, FP64 or FP32), all
+of them in one
 batched context next to each other, each compared node by node with the
 oracle after the same steps (FP64 1e-11, FP32 1e-5 of the domain size) with
 the same step count and status."""
@@ -35,8 +37,22 @@ def _problem(rng):
     if all(p == 1 for p in parts):
         o = 0
     centre = tuple(lo[a] + 0.5 * (hi[a] - lo[a]) for a in range(dim)) + (0.5,) * (3 - dim)
-    kind = rng.integers(0, 3)
-    if kind == 0:
+    kind = rng.integers(0, 5)
+    if kind == 3:
+        # a tabulated density on its own box (clamped outside), values from a
+        # smooth positive function
+        tn = [int(rng.integers(4, 12)) for _ in range(dim)]
+        tlo = [lo[a] - 0.1 for a in range(dim)]
+        thi = [hi[a] + 0.05 for a in range(dim)]
+        axes = [np.linspace(tlo[a], thi[a], tn[a]) for a in range(dim)]
+        G = np.meshgrid(*axes, indexing="ij")
+        phase = rng.uniform(0, 2 * math.pi, size=dim)
+        val = 1.5 + sum(0.6 * np.cos(2.5 * g + ph) for g, ph in zip(G, phase)) / dim
+        mon = W.Monitor(kind="table", table=np.ascontiguousarray(val.T),
+                        tlo=tuple(tlo) + (0.0,) * (3 - dim), thi=tuple(thi) + (1.0,) * (3 - dim))
+    elif kind == 4 and dim == 2:
+        mon = W.Monitor("arclen_burgers", 1.0, [], p0=float(rng.uniform(0.08, 0.2)))
+    elif kind in (0, 4):
         mon = W.random_bumps(rng, dim)
         # centres inside this problem's box
         for t in mon.terms:
@@ -69,6 +85,19 @@ def _problem(rng):
         precision=prec)
 
 
+def _warm_start(rng, p):
+    """|xi|^2/2 plus a small smooth perturbation (a previous steady state
+    stand-in, Sect. 2), or None."""
+    if rng.uniform() < 0.7:
+        return None
+    axes = [np.linspace(p.lo[a], p.hi[a], p.n[a]) for a in range(p.dim)]
+    G = np.meshgrid(*axes, indexing="ij")
+    h2 = min(((p.hi[a] - p.lo[a]) / (p.n[a] - 1)) ** 2 for a in range(p.dim))
+    bump = sum(np.cos(math.pi * (g - p.lo[a]) / (p.hi[a] - p.lo[a])) for a, g in enumerate(G))
+    return np.ascontiguousarray((sum(0.5 * g * g for g in G) + 0.02 * bump *
+                                 (max(p.hi[a] - p.lo[a] for a in range(p.dim)) ** 2) / p.dim).T)
+
+
 def test_random_problems_in_one_batch():
     import torch
     assert torch.cuda.is_available()
@@ -76,12 +105,17 @@ def test_random_problems_in_one_batch():
     build.build()
     pma.load()
     rng = np.random.default_rng(20061460)
-    probs = [_problem(rng) for _ in range(48)]
-    refs = oracle.solve_parallel([p.replace(precision="fp64") for p in probs])
-    res = pma.solve_many(probs, window_steps=16)
+    probs = [_problem(rng) for _ in range(64)]
+    psi0s = [_warm_start(rng, p) for p in probs]
+    refs = oracle.solve_parallel([p.replace(precision="fp64") for p in probs], psi0s=psi0s)
+    with pma.Context(window_steps=16) as ctx:
+        ids = [ctx.submit(p, q) for p, q in zip(probs, psi0s)]
+        ctx.run()
+        res = [ctx.mesh(p, i) for p, i in zip(probs, ids)]
     kinds = set()
     for i, (p, ref, (x, _, info)) in enumerate(zip(probs, refs, res)):
-        kinds.add((p.dim, p.precision, p.alternating, p.exchange_every > 1, p.rhs))
+        kinds.add((p.dim, p.precision, p.alternating, p.exchange_every > 1, p.rhs,
+                   p.monitor.kind))
         if p.precision == "fp64" or ref.status != "tangled":
             assert info.steps == ref.steps, (i, info.steps, ref.steps)
         if p.precision == "fp64":
@@ -90,4 +124,4 @@ def test_random_problems_in_one_batch():
         tol = 1e-11 if p.precision == "fp64" else 1e-5
         if ref.status != "tangled":
             assert np.abs(x - ref.x).max() <= tol * size, (i, np.abs(x - ref.x).max())
-    assert len(kinds) >= 12
+    assert len(kinds) >= 20
