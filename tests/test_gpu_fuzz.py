@@ -125,3 +125,50 @@ def test_random_problems_in_one_batch():
         if ref.status != "tangled":
             assert np.abs(x - ref.x).max() <= tol * size, (i, np.abs(x - ref.x).max())
     assert len(kinds) >= 20
+
+
+def test_random_problems_in_every_execution_mode():
+    """The same random problems through the other execution paths: one
+    launch per subdomain and step without graphs, two request groups on two
+    streams, and graphs off must give the batched path's bits; the
+    cluster-resident path (a different summation order of theta) and the
+    allocation-free entry point must meet the oracle bounds."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2006_14602_gb300 import build
+    build.build()
+    pma.load()
+    rng = np.random.default_rng(1460620)
+    probs = [_problem(rng) for _ in range(24)]
+    refs = oracle.solve_parallel([p.replace(precision="fp64") for p in probs])
+
+    def run(**opts):
+        with pma.Context(window_steps=8, **opts) as ctx:
+            ids = [ctx.submit(p) for p in probs]
+            ctx.run()
+            return [ctx.mesh(p, i) for p, i in zip(probs, ids)]
+
+    base = run()
+    for opts in ({"launch_mode": pma.PMA_LAUNCH_PER_SUBDOMAIN, "use_graphs": 0},
+                 {"groups": 2}, {"use_graphs": 0}):
+        for (a, _, ia), (b, _, ib) in zip(base, run(**opts)):
+            assert ia.steps == ib.steps and ia.status == ib.status, opts
+            np.testing.assert_array_equal(a, b, err_msg=str(opts))
+    for i, (p, ref, (x, _, info)) in enumerate(zip(probs, refs, run(resident=4))):
+        size = max(p.hi[a] - p.lo[a] for a in range(p.dim))
+        tol = 1e-11 if p.precision == "fp64" else 1e-5
+        if ref.status != "tangled":
+            assert info.steps == ref.steps
+            assert np.abs(x - ref.x).max() <= tol * size, (i, "resident")
+    for i, (p, ref) in enumerate(zip(probs, refs)):
+        if ref.status == "tangled":
+            continue
+        g, m, d, q = pma.to_structs(p)
+        out = torch.empty(p.dim * p.nodes, dtype=torch.float64, device="cuda")
+        st, info = pma.pma_solve_static(g, m, d, q, 0, out.data_ptr(), 0)
+        assert st in (pma.PMA_OK, pma.PMA_NOT_CONVERGED), (i, pma.pma_last_error())
+        assert info.steps == ref.steps
+        x = out.cpu().numpy().reshape(ref.x.shape)
+        size = max(p.hi[a] - p.lo[a] for a in range(p.dim))
+        tol = 1e-11 if p.precision == "fp64" else 1e-5
+        assert np.abs(x - ref.x).max() <= tol * size, (i, "static")
