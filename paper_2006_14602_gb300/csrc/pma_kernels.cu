@@ -874,6 +874,43 @@ __device__ __forceinline__ void issue_hdr(const LaunchArgs& a, BandHdr<T>& H, co
   cp_async_commit();
 }
 
+// Thread 0: the pending queue ticket (if any) becomes the following item
+// and its work item is loaded (used at the next item's top).
+__device__ __forceinline__ void resolve_pull(const LaunchArgs& a, int& t_next, WorkItem& w_next,
+                                             int& q_pend, int tend) {
+  if (q_pend < 0) return;
+  t_next = a.t0 + ((a.order == nullptr || q_pend >= a.nwork) ? q_pend : __ldg(a.order + q_pend));
+  if (t_next < tend) w_next = a.work[t_next];
+  q_pend = -1;
+}
+
+// Warp 0 after the per-warp partials are in shared memory: lane q < 7 folds
+// field q of the item's record (theta, the three L2 sums, the extrema of
+// G and min det) over the warps in warp order, lane 7 the non-finite count;
+// each lane stores its field of the 64-byte record.
+template <typename T, int NW>
+__device__ __forceinline__ void write_record(const LaunchArgs& a, int t, int sub, const T* red_t,
+                                             const T* red_f, const int* red_i, int lane) {
+  double* const rec = (double*)(a.part + t);
+  if (lane < 4) {
+    T s = 0;
+    for (int w = 0; w < NW; ++w) s += red_t[lane * NW + w];
+    rec[lane] = (double)s;
+  } else if (lane == 4) {
+    T m = -big_val<T>();
+    for (int w = 0; w < NW; ++w) m = fmax(m, red_f[w]);
+    rec[4] = (double)m;
+  } else if (lane < 7) {
+    T m = big_val<T>();
+    for (int w = 0; w < NW; ++w) m = fmin(m, red_f[(lane - 4) * NW + w]);
+    rec[lane] = (double)m;
+  } else if (lane == 7) {
+    int cnt = 0;
+    for (int w = 0; w < NW; ++w) cnt += red_i[w];
+    *(int2*)(rec + 7) = make_int2(cnt, sub);
+  }
+}
+
 // One work item is a band of `rows` x `cols` nodes of one subdomain (cols a
 // multiple of 4 except at the subdomain's right edge; rows padded to a pitch
 // of 4 elements in memory).  Staging (one pass): the band plus a one-node
@@ -903,6 +940,7 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
   int t_next = 0;
   WorkItem w_next;
   unsigned int tph = 0;  // parity of the TMA barrier's next phase
+  int q_pend = -1;       // thread 0: queue ticket not yet resolved
   if (tid == 0) mbar_init(&tbar, 1);
   __syncthreads();
   if (tid == 0) {
@@ -921,7 +959,7 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
     if (t >= tend) break;
     if (tid == 0) {
       // the band's TMA box first, so that its copy overlaps the prefetch of
-      // the following item (whose queue atomic this thread then waits for)
+      // the following item
       const BandHdr<T>& Hc = HB[b];
       const int pc = Hc.ps.phase;
       if (pc != PH_DONE && pc != PH_INIT_V && a.tmap != nullptr && Hc.w.tma_rows > 0) {
@@ -931,17 +969,22 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
         tma_load_2d(sv, (const char*)a.tmap + 128 * ((size_t)Hc.w.tma_map + Hc.ps.parity),
                     (Hc.w.ij & 0xffff) - 4, (Hc.w.ij >> 16) - 1, &tbar);
       }
-      // publish and prefetch the following item into the other buffer
+      // publish the following item, copy its descriptors into the other
+      // header buffer and take the queue ticket of the item after it
+      // (resolved once this item has been computed, so that the queue
+      // atomic and the loads that depend on it do not hold up the staging)
       s_t[b ^ 1] = t_next;
       if (t_next < tend) {
         issue_hdr<T>(a, HB[b ^ 1], w_next);
-        t_next = pull_item(a);
-        if (t_next < tend) w_next = a.work[t_next];
+        q_pend = (int)atomicAdd(a.queue, 1u);
       }
     }
     BandHdr<T>& H = HB[b];
     const int phase = H.ps.phase;
-    if (phase == PH_DONE) continue;
+    if (phase == PH_DONE) {
+      if (tid == 0) resolve_pull(a, t_next, w_next, q_pend, tend);
+      continue;
+    }
     const int n0 = H.sd.n[0], n1 = H.sd.n[1];
     const long long pitch = H.sd.pitch;
     const int i0 = H.w.ij & 0xffff, j0 = H.w.ij >> 16;
@@ -1233,7 +1276,8 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
       ws = A.ws;
       th = A.th2.x() + A.th2.y();
     }
-    // tile record and arrival
+    if (tid == 0) resolve_pull(a, t_next, w_next, q_pend, tend);
+    // tile record
     th = warp_sum(th);
     if (H.ph.stop_norm == PMA_STOP_L2_INCREMENT) {
       l2a = warp_sum(l2a);
@@ -1253,32 +1297,7 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
       red_i[wid] = nf;
     }
     __syncthreads();  // S3
-    if (tid == 0) {
-      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      T m0 = -big_val<T>(), m1 = big_val<T>(), m2 = big_val<T>();
-      int cnt = 0;
-      for (int w = 0; w < NW; ++w) {
-        s0 += red_t[0 * NW + w];
-        s1 += red_t[1 * NW + w];
-        s2 += red_t[2 * NW + w];
-        s3 += red_t[3 * NW + w];
-        m0 = fmax(m0, red_f[0 * NW + w]);
-        m1 = fmin(m1, red_f[1 * NW + w]);
-        m2 = fmin(m2, red_f[2 * NW + w]);
-        cnt += red_i[w];
-      }
-      Partial rec;
-      rec.theta = (double)s0;
-      rec.l2a = (double)s1;
-      rec.l2b = (double)s2;
-      rec.wsum = (double)s3;
-      rec.gmax = (double)m0;
-      rec.gmin = (double)m1;
-      rec.dmin = (double)m2;
-      rec.nonfinite = cnt;
-      rec.sub = H.w.sub;
-      a.part[t] = rec;
-    }
+    if (wid == 0) write_record<T, NW>(a, t, H.w.sub, red_t, red_f, red_i, lane);
   }
   if (tid == 0) queue_exit(a);
   // this CTA has run out of work: the next kernel of the stream (launched
@@ -1695,6 +1714,7 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
   int t_next = 0;
   WorkItem w_next;
   unsigned int tph = 0;  // parity of the TMA barrier's next phase
+  int q_pend = -1;       // thread 0: queue ticket not yet resolved
   if (tid == 0) mbar_init(&tbar, 1);
   __syncthreads();
   if (tid == 0) {
@@ -1713,7 +1733,7 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
     if (t >= tend) break;
     if (tid == 0) {
       // the box's TMA copy first, so that it overlaps the prefetch of the
-      // following item (whose queue atomic this thread then waits for)
+      // following item
       const SmemHdr<T>& Hc = HB[b];
       const int pc = Hc.ps.phase;
       if (pc != PH_DONE && pc != PH_INIT_V && a.tmap != nullptr && Hc.w.tma_rows > 0) {
@@ -1727,13 +1747,15 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
       s_t[b ^ 1] = t_next;
       if (t_next < tend) {
         issue_hdr<T>(a, HB[b ^ 1], w_next);
-        t_next = pull_item(a);
-        if (t_next < tend) w_next = a.work[t_next];
+        q_pend = (int)atomicAdd(a.queue, 1u);
       }
     }
     SmemHdr<T>& H = HB[b];
     const int phase = H.ps.phase;
-    if (phase == PH_DONE) continue;
+    if (phase == PH_DONE) {
+      if (tid == 0) resolve_pull(a, t_next, w_next, q_pend, tend);
+      continue;
+    }
     const int n0 = H.sd.n[0], n1 = H.sd.n[1], n2 = H.sd.n[2];
     const long long pitch = H.sd.pitch, ppitch = pitch * n1;
     const int i0 = H.w.ij & 0xffff, j0 = H.w.ij >> 16;
@@ -2116,6 +2138,7 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
       ws = A.ws;
       th = A.th2.x() + A.th2.y();
     }
+    if (tid == 0) resolve_pull(a, t_next, w_next, q_pend, tend);
     // tile record
     th = warp_sum(th);
     if (H.ph.stop_norm == PMA_STOP_L2_INCREMENT) {
@@ -2136,32 +2159,7 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
       red_i[wid] = nf;
     }
     __syncthreads();
-    if (tid == 0) {
-      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      T m0 = -big_val<T>(), m1 = big_val<T>(), m2 = big_val<T>();
-      int cnt = 0;
-      for (int w = 0; w < NW; ++w) {
-        s0 += red_t[0 * NW + w];
-        s1 += red_t[1 * NW + w];
-        s2 += red_t[2 * NW + w];
-        s3 += red_t[3 * NW + w];
-        m0 = fmax(m0, red_f[0 * NW + w]);
-        m1 = fmin(m1, red_f[1 * NW + w]);
-        m2 = fmin(m2, red_f[2 * NW + w]);
-        cnt += red_i[w];
-      }
-      Partial rec;
-      rec.theta = (double)s0;
-      rec.l2a = (double)s1;
-      rec.l2b = (double)s2;
-      rec.wsum = (double)s3;
-      rec.gmax = (double)m0;
-      rec.gmin = (double)m1;
-      rec.dmin = (double)m2;
-      rec.nonfinite = cnt;
-      rec.sub = H.w.sub;
-      a.part[t] = rec;
-    }
+    if (wid == 0) write_record<T, NW>(a, t, H.w.sub, red_t, red_f, red_i, lane);
   }
   if (tid == 0) queue_exit(a);
   // this CTA has run out of work: the next kernel of the stream (launched
