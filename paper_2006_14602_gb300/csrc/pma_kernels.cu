@@ -921,16 +921,38 @@ __device__ __forceinline__ void write_record(const LaunchArgs& a, int t, int sub
 // and writes the 4 results with one 16-byte store.  Shared row layout: node
 // column c sits at c + 4 (halo columns at 3 and cols + 4), rows are `SWp`
 // (a multiple of 4) wide.
-template <typename T, int NT, int SMAX, int MB>
+// Thread 0: the TMA box of the item whose header is H (its staged rows,
+// SWp columns wide) into buffer sv, completing on barrier bar; false when
+// the item is staged otherwise (done, first pass, or no tensor map).
+template <typename T>
+__device__ __forceinline__ bool issue_box2d(const LaunchArgs& a, const SmemHdr<T>& H, T* sv,
+                                            unsigned long long* bar) {
+  const int pc = H.ps.phase;
+  if (pc == PH_DONE || pc == PH_INIT_V || a.tmap == nullptr || H.w.tma_rows <= 0) return false;
+  const int swp = (((H.w.ext & 0xffff) + 3) & ~3) + 8;
+  fence_proxy_async();
+  mbar_expect_tx(bar, (unsigned int)(swp * H.w.tma_rows * (int)sizeof(T) + a.stall_bytes));
+  tma_load_2d(sv, (const char*)a.tmap + 128 * ((size_t)H.w.tma_map + H.ps.parity),
+              (H.w.ij & 0xffff) - 4, (H.w.ij >> 16) - 1, bar);
+  return true;
+}
+
+template <typename T, int NT, int SMAX, int MB, bool PF>
 __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
   // programmatic dependent launch: wait until the preceding kernel of the
   // stream has completed and its writes are visible
   asm volatile("griddepcontrol.wait;" ::: "memory");
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int NW = NT / 32;
-  __shared__ __align__(128) T sv[SMAX];
+  // PF: two band buffers; the following item's box is loaded into the
+  // other one while this item is computed.  A TMA destination in shared
+  // memory must be 128-byte aligned, so the buffer stride SB is SMAX
+  // rounded up to 128 bytes.
+  constexpr int SB = (SMAX + 128 / (int)sizeof(T) - 1) / (128 / (int)sizeof(T)) * (128 / (int)sizeof(T));
+  static_assert((SB * sizeof(T)) % 128 == 0, "band buffers start on 128-byte boundaries");
+  __shared__ __align__(128) T sv_all[PF ? 2 * SB : SMAX];
   __shared__ __align__(16) BandHdr<T> HB[2];
-  __shared__ __align__(8) unsigned long long tbar;  // TMA staging barrier
+  __shared__ __align__(8) unsigned long long tbar_all[2];  // TMA staging barriers
   __shared__ int s_t[2];
   __shared__ T red_t[4 * NW];
   __shared__ T red_f[3 * NW];
@@ -939,9 +961,13 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
   const int tend = a.t0 + a.nwork;
   int t_next = 0;
   WorkItem w_next;
-  unsigned int tph = 0;  // parity of the TMA barrier's next phase
-  int q_pend = -1;       // thread 0: queue ticket not yet resolved
-  if (tid == 0) mbar_init(&tbar, 1);
+  unsigned int tphs = 0;  // bit k: parity of barrier k's next phase
+  int q_pend = -1;        // thread 0: queue ticket not yet resolved
+  bool ahead = false;     // thread 0: the current item's box was issued ahead
+  if (tid == 0) {
+    mbar_init(&tbar_all[0], 1);
+    mbar_init(&tbar_all[1], 1);
+  }
   __syncthreads();
   if (tid == 0) {
     const int t0 = pull_item(a);
@@ -957,18 +983,14 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
     __syncthreads();  // S1: header `b` complete and visible
     const int t = s_t[b];
     if (t >= tend) break;
+    const int bb = PF ? b : 0;  // band buffer and barrier of this item
+    T* const sv = sv_all + bb * SB;
+    unsigned long long* const tbar = &tbar_all[bb];
     if (tid == 0) {
-      // the band's TMA box first, so that its copy overlaps the prefetch of
-      // the following item
-      const BandHdr<T>& Hc = HB[b];
-      const int pc = Hc.ps.phase;
-      if (pc != PH_DONE && pc != PH_INIT_V && a.tmap != nullptr && Hc.w.tma_rows > 0) {
-        const int swp = (((Hc.w.ext & 0xffff) + 3) & ~3) + 8;
-        fence_proxy_async();
-        mbar_expect_tx(&tbar, (unsigned int)(swp * Hc.w.tma_rows * (int)sizeof(T) + a.stall_bytes));
-        tma_load_2d(sv, (const char*)a.tmap + 128 * ((size_t)Hc.w.tma_map + Hc.ps.parity),
-                    (Hc.w.ij & 0xffff) - 4, (Hc.w.ij >> 16) - 1, &tbar);
-      }
+      // the band's TMA box first (unless it was issued ahead), so that its
+      // copy overlaps the prefetch of the following item
+      if (!ahead) issue_box2d<T>(a, HB[b], sv, tbar);
+      ahead = false;
       // publish the following item, copy its descriptors into the other
       // header buffer and take the queue ticket of the item after it
       // (resolved once this item has been computed, so that the queue
@@ -1144,15 +1166,15 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
       cp_async_wait_all();
       bool gave_up = false;
       if (tr > 0) {
-        gave_up = !mbar_wait(&tbar, tph);
-        tph ^= 1;
+        gave_up = !mbar_wait(tbar, (tphs >> bb) & 1u);
+        tphs ^= 1u << bb;
       }
       if (__syncthreads_or(gave_up)) {
         // the box never arrived: report, give the copy one more bounded
         // wait, and leave (the host turns the error word into a status)
         if (tid == 0) {
           atomicOr(a.err, 1u);
-          mbar_wait(&tbar, tph ^ 1);
+          mbar_wait(tbar, ((tphs >> bb) & 1u) ^ 1u);
         }
         break;
       }
@@ -1208,6 +1230,12 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
         stage_alternating<T, NT>(a, H, sv, SWp, SH, 1, i0, j0, 0, cols);
       }
       __syncthreads();  // S2: band staged
+      if (PF && tid == 0 && t_next < tend) {
+        // the following item's box into the other buffer (its header was
+        // requested at this item's top; the buffer's last item is done)
+        cp_async_wait_all();
+        ahead = issue_box2d<T>(a, HB[b ^ 1], sv_all + (bb ^ 1) * SB, &tbar_all[bb ^ 1]);
+      }
       if (phase == PH_RUN && !exch) {
         // interface data frozen between exchanges: every transmission node
         // of the band keeps the value it was staged with (offset included)
@@ -2173,9 +2201,11 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
 // for; FP64 budgets for 4): the staged band plus halo and the column
 // tables fit in nodes x factor / 10 elements (bands get fewer rows, or
 // narrower strips, where the halo would not fit).
-#define PMA_T2D(X) X(128, 3072, 1536, 16, 7) X(128, 2048, 1024, 30, 7) \
-                   X(128, 4096, 2048, 14, 7) X(128, 5120, 2560, 14, 7) \
-                   X(128, 768, 384, 30, 7) X(128, 6144, 3072, 14, 6) X(128, 4096, 2048, 14, 6)
+#define PMA_T2D(X) X(128, 3072, 1536, 16, 7, 0) X(128, 2048, 1024, 30, 7, 0) \
+                   X(128, 4096, 2048, 14, 7, 0) X(128, 5120, 2560, 14, 7, 0) \
+                   X(128, 768, 384, 30, 7, 0) X(128, 6144, 3072, 14, 6, 0) \
+                   X(128, 4096, 2048, 14, 6, 0) X(128, 4096, 2048, 14, 4, 1) \
+                   X(128, 3072, 1536, 16, 5, 1) X(128, 2048, 1024, 16, 8, 1)
 #define PMA_SMAX(n, f) (((n) * (f) / 10) & ~3)
 // 3D: (threads, nodes per plane box, planes FP32, planes FP64, dynamic
 // shared memory in KiB for the staged box and the column tables, FP32 CTAs
@@ -2184,7 +2214,7 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
                    X(128, 512, 8, 4, 32, 5) X(128, 512, 8, 4, 32, 6)
 
 static const int k_t2d[][4] = {
-#define E(a, b, c, f, m) {a, b, c, f},
+#define E(a, b, c, f, m, pf) {a, b, c, f},
     PMA_T2D(E)
 #undef E
 };
@@ -2224,13 +2254,13 @@ static const void* sweep_fn(int dim, int id, int* nthreads, int* dyn) {
   int k = 0;
   *dyn = 0;
   if (dim == 2) {
-#define E(a, b, c, f, m)                                                   \
+#define E(a, b, c, f, m, pf)                                               \
   if (k++ == id) {                                                         \
     *nthreads = (a);                                                       \
     if constexpr (sizeof(T) == 8)                                          \
-      return (const void*)k_band2d<T, a, PMA_SMAX(c, f), 512 / (a)>;       \
+      return (const void*)k_band2d<T, a, PMA_SMAX(c, f), 512 / (a), pf>;   \
     else                                                                   \
-      return (const void*)k_band2d<T, a, PMA_SMAX(b, f), m>;               \
+      return (const void*)k_band2d<T, a, PMA_SMAX(b, f), m, pf>;           \
   }
     PMA_T2D(E)
 #undef E
