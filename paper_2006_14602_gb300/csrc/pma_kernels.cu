@@ -1230,11 +1230,13 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
         stage_alternating<T, NT>(a, H, sv, SWp, SH, 1, i0, j0, 0, cols);
       }
       __syncthreads();  // S2: band staged
-      if (PF && tid == 0 && t_next < tend) {
-        // the following item's box into the other buffer (its header was
-        // requested at this item's top; the buffer's last item is done)
-        cp_async_wait_all();
-        ahead = issue_box2d<T>(a, HB[b ^ 1], sv_all + (bb ^ 1) * SB, &tbar_all[bb ^ 1]);
+      if constexpr (PF) {
+        if (tid == 0 && t_next < tend) {
+          // the following item's box into the other buffer (its header was
+          // requested at this item's top; the buffer's last item is done)
+          cp_async_wait_all();
+          ahead = issue_box2d<T>(a, HB[b ^ 1], sv_all + (bb ^ 1) * SB, &tbar_all[bb ^ 1]);
+        }
       }
       if (phase == PH_RUN && !exch) {
         // interface data frozen between exchanges: every transmission node
