@@ -327,9 +327,10 @@ pma_status pma_get_mesh_device_batch(pma_ctx *ctx, int32_t n, const uint64_t *id
 /* Batched pma_get_mesh into ONE caller-owned HOST buffer: the meshes of the
  * n finished requests ids[0..n-1] are packed back to back in that order,
  * request i's dim_i * N_i doubles (component-major) starting right after
- * request i-1's.  One combination launch and one device-to-host copy for the
- * whole batch (fastest into page-locked memory, e.g. cudaHostAlloc or
- * cudaHostRegister; pageable memory works too).  infos (optional) receives n
+ * request i-1's.  Into page-locked memory (cudaHostAlloc, cudaHostRegister)
+ * one combination launch writes the meshes directly through the buffer's
+ * device mapping; into pageable memory one combination launch into a
+ * device staging buffer and one device-to-host copy.  infos (optional) receives n
  * records.  Releases the requests.  Errors (nothing is released):
  * PMA_ERR_NOT_FOUND (unknown id), PMA_ERR_BUSY (a request not finished or
  * without a mesh), PMA_ERR_INVALID (NULL buffers, an id listed twice),

@@ -2042,16 +2042,30 @@ pma_status pma_get_mesh_batch(pma_ctx* c, int32_t n, const uint64_t* ids, double
     off.push_back(total);
     total += (size_t)r.dim * (size_t)r.nodes;
   }
-  if (total > c->stage_cap) {
+  // Page-locked host memory is mapped into the device's address space: the
+  // combination kernel then writes the meshes straight into it (all SMs
+  // writing over the host link, no staging buffer and no separate copy).
+  // Pageable memory goes through a device staging buffer and one copy.
+  double* direct = nullptr;
+  {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, x_out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer != nullptr)
+      direct = (double*)pa.devicePointer;
+    else
+      cudaGetLastError();  // an unregistered pointer is not an error here
+  }
+  if (!direct && total > c->stage_cap) {
     cudaFree(c->d_stage);
     c->d_stage = nullptr;
     c->stage_cap = 0;
     PMA_CK(cudaMalloc(&c->d_stage, sizeof(double) * total));
     c->stage_cap = total;
   }
+  double* const dst = direct ? direct : c->d_stage;
   std::vector<CombineJob> jobs;
   for (int i = 0; i < n; ++i) {
-    jobs.push_back(CombineJob{rs[i]->slot, 1, c->d_stage + off[i], nullptr, blocks});
+    jobs.push_back(CombineJob{rs[i]->slot, 1, dst + off[i], nullptr, blocks});
     blocks += (rs[i]->nodes + kCombineNodes - 1) / kCombineNodes;
   }
   if (c->dirty) {
@@ -2063,8 +2077,9 @@ pma_status pma_get_mesh_batch(pma_ctx* c, int32_t n, const uint64_t* ids, double
   PMA_CK(cudaMemcpyAsync(c->d_jobs, jobs.data(), sizeof(CombineJob) * jobs.size(),
                          cudaMemcpyHostToDevice, c->stream));
   PMA_CK(launch_combine(c->d_jobs, n, blocks, c->d_subs, c->d_probs, c->d_state, c->stream));
-  PMA_CK(cudaMemcpyAsync(x_out, c->d_stage, sizeof(double) * total, cudaMemcpyDeviceToHost,
-                         c->stream));
+  if (!direct)
+    PMA_CK(cudaMemcpyAsync(x_out, c->d_stage, sizeof(double) * total, cudaMemcpyDeviceToHost,
+                           c->stream));
   PMA_CK(cudaStreamSynchronize(c->stream));
   c->stats.h2d_bytes += (double)sizeof(CombineJob) * jobs.size();
   c->stats.d2h_bytes += (double)sizeof(double) * total;
