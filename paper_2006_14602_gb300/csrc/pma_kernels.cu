@@ -480,10 +480,19 @@ __device__ __forceinline__ TrBox3 tr_box3(int dlx, int dhx, int dly, int dhy, in
 // counters for the next launch.  The partial record
 // of an item is indexed by the item, so results do not depend on which CTA
 // took it.
-__device__ __forceinline__ int pull_item(const LaunchArgs& a) {
-  const int q = (int)atomicAdd(a.queue, 1u);
+// The first grid positions of the order go to the CTAs statically (CTA b
+// starts with position b, without the queue, so that it can fetch that item
+// before the preceding launch has finished); the counter hands out the
+// positions after them.
+__device__ __forceinline__ int item_of_pos(const LaunchArgs& a, int q) {
   if (a.order == nullptr || q >= a.nwork) return a.t0 + q;
   return a.t0 + __ldg(a.order + q);
+}
+__device__ __forceinline__ int queue_ticket(const LaunchArgs& a) {
+  return (int)atomicAdd(a.queue, 1u) + (int)gridDim.x;
+}
+__device__ __forceinline__ int pull_item(const LaunchArgs& a) {
+  return item_of_pos(a, queue_ticket(a));
 }
 __device__ __forceinline__ void queue_exit(const LaunchArgs& a) {
   __threadfence();
@@ -862,6 +871,26 @@ __device__ __forceinline__ void stencil_core4(const RunK<T>& K, const MonT<T>& m
 template <typename T>
 using BandHdr = SmemHdr<T>;
 
+// The first item's descriptors in two parts: the work item, subdomain and
+// problem descriptors (unchanged within a window) before the wait for the
+// preceding launch, the problem state (which the finish pass writes) after
+// it.
+template <typename T>
+__device__ __forceinline__ void issue_hdr_static(const LaunchArgs& a, BandHdr<T>& H,
+                                                 const WorkItem& w) {
+  H.w = w;
+  const char* s0 = (const char*)(a.subs + w.sub);
+  const char* s2 = (const char*)(hot_table<T>(a) + w.prob);
+  for (int i = 0; i < (int)(sizeof(SubDesc) / 16); ++i) cp_async16((char*)&H.sd + 16 * i, s0 + 16 * i);
+  for (int i = 0; i < (int)(sizeof(ProbHot<T>) / 16); ++i) cp_async16((char*)&H.ph + 16 * i, s2 + 16 * i);
+}
+template <typename T>
+__device__ __forceinline__ void issue_hdr_state(const LaunchArgs& a, BandHdr<T>& H, int prob) {
+  const char* s1 = (const char*)(a.st + prob);
+  for (int i = 0; i < (int)(sizeof(ProbState) / 16); ++i) cp_async16((char*)&H.ps + 16 * i, s1 + 16 * i);
+  cp_async_commit();
+}
+
 template <typename T>
 __device__ __forceinline__ void issue_hdr(const LaunchArgs& a, BandHdr<T>& H, const WorkItem& w) {
   H.w = w;
@@ -879,7 +908,7 @@ __device__ __forceinline__ void issue_hdr(const LaunchArgs& a, BandHdr<T>& H, co
 __device__ __forceinline__ void resolve_pull(const LaunchArgs& a, int& t_next, WorkItem& w_next,
                                              int& q_pend, int tend) {
   if (q_pend < 0) return;
-  t_next = a.t0 + ((a.order == nullptr || q_pend >= a.nwork) ? q_pend : __ldg(a.order + q_pend));
+  t_next = item_of_pos(a, q_pend);
   if (t_next < tend) w_next = a.work[t_next];
   q_pend = -1;
 }
@@ -939,9 +968,6 @@ __device__ __forceinline__ bool issue_box2d(const LaunchArgs& a, const SmemHdr<T
 
 template <typename T, int NT, int SMAX, int MB, bool PF>
 __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
-  // programmatic dependent launch: wait until the preceding kernel of the
-  // stream has completed and its writes are visible
-  asm volatile("griddepcontrol.wait;" ::: "memory");
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int NW = NT / 32;
   // PF: two band buffers; the following item's box is loaded into the
@@ -968,11 +994,21 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
     mbar_init(&tbar_all[0], 1);
     mbar_init(&tbar_all[1], 1);
   }
+  // Before the wait for the preceding kernel of the stream (programmatic
+  // dependent launch): this CTA's first item (its static position in the
+  // order) and the descriptors that no launch of a window writes.
+  int t0 = tend;
+  if (tid == 0) {
+    t0 = item_of_pos(a, (int)blockIdx.x);
+    s_t[0] = t0;
+    if (t0 < tend) issue_hdr_static<T>(a, HB[0], a.work[t0]);
+  }
+  // wait until the preceding kernel has completed and its writes are
+  // visible; then the first item's state and the following item
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
   if (tid == 0) {
-    const int t0 = pull_item(a);
-    s_t[0] = t0;
-    if (t0 < tend) issue_hdr<T>(a, HB[0], a.work[t0]);
+    if (t0 < tend) issue_hdr_state<T>(a, HB[0], HB[0].w.prob);
     t_next = pull_item(a);
     if (t_next < tend) w_next = a.work[t_next];
   }
@@ -998,7 +1034,7 @@ __global__ void __launch_bounds__(NT, MB) k_band2d(LaunchArgs a) {
       s_t[b ^ 1] = t_next;
       if (t_next < tend) {
         issue_hdr<T>(a, HB[b ^ 1], w_next);
-        q_pend = (int)atomicAdd(a.queue, 1u);
+        q_pend = queue_ticket(a);
       }
     }
     BandHdr<T>& H = HB[b];
@@ -1725,9 +1761,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT) k_res2
 // values of the 19-point stencils of its 4 nodes with aligned vector loads.
 template <typename T, int NT, int TZ, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
-  // programmatic dependent launch: wait until the preceding kernel of the
-  // stream has completed and its writes are visible
-  asm volatile("griddepcontrol.wait;" ::: "memory");
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int NW = NT / 32;
   constexpr int HMAX = 8;  // halo rows per thread (host: (rows+2)(TZ+2) <= 8 NT)
@@ -1746,11 +1779,21 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
   unsigned int tph = 0;  // parity of the TMA barrier's next phase
   int q_pend = -1;       // thread 0: queue ticket not yet resolved
   if (tid == 0) mbar_init(&tbar, 1);
+  // Before the wait for the preceding kernel of the stream (programmatic
+  // dependent launch): this CTA's first item (its static position in the
+  // order) and the descriptors that no launch of a window writes.
+  int t0 = tend;
+  if (tid == 0) {
+    t0 = item_of_pos(a, (int)blockIdx.x);
+    s_t[0] = t0;
+    if (t0 < tend) issue_hdr_static<T>(a, HB[0], a.work[t0]);
+  }
+  // wait until the preceding kernel has completed and its writes are
+  // visible; then the first item's state and the following item
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
   if (tid == 0) {
-    const int t0 = pull_item(a);
-    s_t[0] = t0;
-    if (t0 < tend) issue_hdr<T>(a, HB[0], a.work[t0]);
+    if (t0 < tend) issue_hdr_state<T>(a, HB[0], HB[0].w.prob);
     t_next = pull_item(a);
     if (t_next < tend) w_next = a.work[t_next];
   }
@@ -1777,7 +1820,7 @@ __global__ void __launch_bounds__(NT, MINB) k_band3d(LaunchArgs a) {
       s_t[b ^ 1] = t_next;
       if (t_next < tend) {
         issue_hdr<T>(a, HB[b ^ 1], w_next);
-        q_pend = (int)atomicAdd(a.queue, 1u);
+        q_pend = queue_ticket(a);
       }
     }
     SmemHdr<T>& H = HB[b];
